@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Benchmark of the compressed 3-vector add (the paper's Sec. 5 test, C = A + B)
+on GB300, through the library's C ABI.
+
+One step = one fused launch c = compress(decompress(a) + decompress(b)) over
+N = 2^28 packed <0,7,22>-17-18 words per GPU (magnitudes 10^U(-3,3), uniform
+directions), inputs resident in HBM.  Printed: one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ivc|reference]
+
+Under torchrun (N > 1) each rank processes its own N = 2^28 shard (weak
+scaling, no data-path collective); the time is the maximum over ranks.
+``--impl reference`` times the oracle (plain CPU reference) on the host cores
+on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compressed 3-vector add: Gvec/s and % HBM peak vs FP32x3 at stated error"
+UNIT = "Gvec/s"
+BYTES_PER_VEC = 24          # read two 8-byte words, write one
+FP32_BYTES_PER_VEC = 36     # read two 12-byte vectors, write one
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ivc", "reference"], default="ivc")
+    p.add_argument("--log2n", type=int, default=28)
+    p.add_argument("--no-extra", action="store_true", help="skip the baseline/extra measurements")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2003_02633_gb300", "csrc", "*")))
+    files.append(os.path.join(ROOT, "include", "ivc.h"))
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy, burst)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+
+
+def ncu_traffic(kernel: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_vector"]) * n
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value: float, device) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- helpers
+
+def time_launches(fn, steps, warmup, stream, sync_all=None):
+    """Warm-up, then time exactly `steps` launches with CUDA events on
+    `stream`.  Returns (total_ms, per_launch_ms list)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if sync_all:
+        sync_all()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if sync_all:
+        sync_all()
+    return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev]
+
+
+def run_ivc(args):
+    import numpy as np
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ivc.load()
+    n = 1 << args.log2n
+    fmt = ivc.default_format()
+    stream = torch.cuda.current_stream()
+    s_handle = stream.cuda_stream
+
+    # Inputs: FP32 AoS vectors drawn on the device, compressed once (untimed).
+    a = synth.device_vectors(n, seed=2 * rank, device=dev)
+    b = synth.device_vectors(n, seed=2 * rank + 1, device=dev)
+    wa = ivc.compress(fmt, a)
+    wb = ivc.compress(fmt, b)
+    wc = torch.empty_like(wa)
+    torch.cuda.synchronize()
+
+    def step():
+        ivc.add(fmt, wa, wb, out=wc, stream=s_handle)
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    # warm-up outside the clock window
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    if sampler:
+        sampler.start()
+    total_ms, per = time_launches(step, args.steps, 0, stream, lambda: barrier(pg))
+    clocks = sampler.stop() if sampler else None
+    total_ms = max_over_ranks(pg, total_ms, dev)
+    ms_step = total_ms / args.steps
+    kernel_ms = statistics.mean(per)
+    value = world * n / (ms_step * 1e-3) / 1e9
+    hbm_peak, peak_src = measured_peaks()
+    achieved = BYTES_PER_VEC * n / (kernel_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("ivc_add", n)
+
+    # End to end through the public API: pinned host words in, result out.
+    h_a = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    h_b = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    h_c = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    h_a.copy_(wa)
+    h_b.copy_(wb)
+    da, db, dc = torch.empty_like(wa), torch.empty_like(wb), torch.empty_like(wc)
+
+    def e2e_step():
+        da.copy_(h_a, non_blocking=True)
+        db.copy_(h_b, non_blocking=True)
+        ivc.add(fmt, da, db, out=dc, stream=s_handle)
+        h_c.copy_(dc, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_ms, _ = time_launches(e2e_step, e2e_steps, 2, stream, lambda: barrier(pg))
+    e2e_ms = max_over_ranks(pg, e2e_ms, dev) / e2e_steps
+    e2e_value = world * n / (e2e_ms * 1e-3) / 1e9
+    del da, db, dc
+    same = bool(torch.equal(h_c, wc.cpu()))
+
+    extra = {}
+    if not args.no_extra:
+        extra = run_extras(args, fmt, a, b, wa, wb, stream, s_handle, n, pg, dev, value)
+
+    cpu = None
+    if rank == 0:
+        cpu = cpu_baseline(args, a, b, wc, fmt)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded torch.Generator on device; uniform directions, "
+                    "magnitudes 10^U(-3,3))",
+            "config": {"workload": f"compressed vector add c = a + b, N = 2^{args.log2n} "
+                                   f"3-vectors per GPU, <0,7,22>-17-18 words (Sec. 5)",
+                       "n_per_gpu": n, "format": "<0,7,22>-17-18, b7=80",
+                       "l2": "inputs larger than L2 (16 B read per vector, "
+                             f"{16 * n / 2**30:.1f} GiB per launch)",
+                       "parallelism": f"dp{world} (independent shards)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                         "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                         "traffic": traffic, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": BYTES_PER_VEC * n,
+                         "kernel_ms": round(kernel_ms, 5)},
+            "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
+                    "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
+                    "matches_device_result": same},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_extras(args, fmt, a, b, wa, wb, stream, s_handle, n, pg, dev, value):
+    """Baselines and the other fused operations at the same N (not the headline)."""
+    import torch
+
+    from paper_2003_02633_gb300 import ivc
+    steps = max(5, min(args.steps, 50))
+    out = {}
+
+    def t(fn):
+        ms, per = time_launches(fn, steps, 3, stream, lambda: barrier(pg))
+        return max_over_ranks(pg, ms / steps, dev), statistics.mean(per)
+
+    c32 = torch.empty_like(a)
+    ms, _ = t(lambda: ivc.f32_add(a, b, out=c32, stream=s_handle))
+    out["fp32_aos_add_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+    out["fp32_aos_add_gbs"] = round(FP32_BYTES_PER_VEC * n / (ms * 1e-3) / 1e9, 1)
+    ms, _ = t(lambda: ivc.f32_add(a, b, out=c32, layout=ivc.IVC_SOA, ld=n, n=n, stream=s_handle))
+    out["fp32_soa_add_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+    out["speedup_vs_fp32_aos"] = round(value / max(out["fp32_aos_add_gvec_s"], 1e-9), 4)
+    out["speedup_vs_fp32_soa"] = round(value / max(out["fp32_soa_add_gvec_s"], 1e-9), 4)
+    del c32
+    y = wb.clone()
+    ms, kms = t(lambda: ivc.axpy(fmt, 0.7, wa, y, stream=s_handle))
+    out["axpy_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+    out["axpy_gbs"] = round(BYTES_PER_VEC * n / (kms * 1e-3) / 1e9, 1)
+    del y
+    y32 = b.clone()
+    ms, _ = t(lambda: ivc.f32_axpy(0.7, a, y32, stream=s_handle))
+    out["fp32_aos_axpy_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+    del y32
+    for kind, name in ((ivc.IVC_F16, "fp16"), (ivc.IVC_BF16, "bf16")):
+        ha = ivc.half_from_f32(kind, a)
+        hb = ivc.half_from_f32(kind, b)
+        hc = torch.empty_like(ha)
+        ms, _ = t(lambda: ivc.half_add(kind, ha, hb, out=hc, stream=s_handle))
+        out[f"{name}_aos_add_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+        del ha, hb, hc
+    # decompress and compress alone (12 B <-> 8 B per vector)
+    d = torch.empty_like(a)
+    ms, _ = t(lambda: ivc.decompress(fmt, wa, out=d, stream=s_handle))
+    out["decompress_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+    cw = torch.empty_like(wa)
+    ms, _ = t(lambda: ivc.compress(fmt, a, out=cw, stream=s_handle))
+    out["compress_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+    del d, cw
+    torch.cuda.synchronize()
+    return out
+
+
+def cpu_baseline(args, a, b, wc, fmt):
+    """The oracle's add on a bounded sample of the same workload, on the host
+    cores (single thread), plus agreement of its words with the GPU's."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    n = a.shape[0]
+    rng = np.random.default_rng(123)
+    chunk = 1 << 14
+    done, secs, mism = 0, 0.0, 0
+    while secs < args.cpu_seconds and done < n:
+        s = int(rng.integers(0, max(1, n - chunk)))
+        av = a[s:s + chunk].cpu().numpy()
+        bv = b[s:s + chunk].cpu().numpy()
+        wa, wb = O.compress(O.PRIMARY, av), O.compress(O.PRIMARY, bv)
+        t0 = time.perf_counter()
+        c = O.add(O.PRIMARY, wa, wb)
+        secs += time.perf_counter() - t0
+        got = wc[s:s + chunk].cpu().numpy().view(np.uint64)
+        mism += int(np.sum(got != c))
+        done += chunk
+    return {"value": round(done / secs / 1e9, 8), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} vectors ({done // chunk} random contiguous slices of {chunk}) of "
+                      f"the same N = 2^{args.log2n} workload, oracle add timed, single thread",
+            "seconds": round(secs, 2), "sample_word_mismatches_vs_gpu": mism}
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args):
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2003_02633_gb300 import synth
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    O.build()
+    # size each step's sample so the whole run takes about a minute
+    probe_a = synth.bandwidth_vectors(4096, seed=0)
+    probe_b = synth.bandwidth_vectors(4096, seed=1)
+    pa, pb = O.compress(O.PRIMARY, probe_a), O.compress(O.PRIMARY, probe_b)
+    t0 = time.perf_counter()
+    O.add(O.PRIMARY, pa, pb)
+    rate = 4096 / (time.perf_counter() - t0)
+    per_step_s = min(2.0, max(0.01, 60.0 / max(1, args.steps + args.warmup)))
+    m = int(max(1024, min(1 << 22, rate * per_step_s)))
+    av = synth.bandwidth_vectors(m, seed=0)
+    bv = synth.bandwidth_vectors(m, seed=1)
+    wa, wb = O.compress(O.PRIMARY, av), O.compress(O.PRIMARY, bv)
+    for _ in range(args.warmup):
+        O.add(O.PRIMARY, wa, wb)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.add(O.PRIMARY, wa, wb)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    value = m / sec / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (binary128 near boundaries)",
+            "data": "synthetic (seeded numpy PCG64; uniform directions, magnitudes 10^U(-3,3))",
+            "config": {"workload": f"compressed vector add c = a + b, bounded samples of the "
+                                   f"N = 2^{args.log2n} workload", "sample_per_step": m,
+                       "format": "<0,7,22>-17-18, b7=80"},
+            "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{m} vectors per step, single thread"},
+            "e2e": {"value": round(value, 8), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ivc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,235 @@
+/*
+ * ivc.h -- C ABI of the GB300 (sm_103a) inline 3-vector compression library.
+ *
+ * Method: Trojak & Witherden, "Inline Vector Compression for Computational
+ * Physics" (arXiv:2003.02633).  A single-precision 3-vector (12 bytes) is
+ * stored in one 64-bit word: the magnitude r = |x| in a reduced float format
+ * and the spherical angles theta = atan2(y, x), phi = acos(z / r) quantised to
+ * integers (Sec. 2.1, Eq. cart2sphere / a_disc / a_inv; Sec. 2.3 magnitude
+ * format; Fig. comp_regimes bit layouts).  The fused kernels decompress,
+ * apply an FP32 elementwise operation and recompress (Sec. 5).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked "device" are device (or managed) memory of the current
+ *     CUDA device; the caller owns every buffer.  Entry points allocate
+ *     nothing per call; the first call with a given format on a device builds
+ *     that format's small trigonometric tables once and keeps them until
+ *     ivc_release_tables() or process exit.
+ *   - Packed words are uint64_t, 8-byte aligned.  FP32 arrays are 4-byte
+ *     aligned.  Wider (16-byte) vector accesses are used when pointers and
+ *     sizes allow; other alignments take a scalar path.
+ *   - Every call is asynchronous on `stream` (NULL = the legacy default
+ *     stream) and returns a status: IVC_OK, or an error for bad arguments,
+ *     a bad format, misaligned pointers or a failed launch.  No call aborts or
+ *     traps.  n == 0 returns IVC_OK without launching.
+ *   - Elementwise operations may run in place (c == a, y updated in place,
+ *     v_out == v); partially overlapping ranges are not allowed.
+ *   - Results do not depend on launch configuration.
+ */
+#ifndef IVC_H
+#define IVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ivc_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  IVC_OK = 0,
+  IVC_ERR_ARG = 1,        /* null pointer with n > 0, n < 0, bad enum value  */
+  IVC_ERR_FORMAT = 2,     /* invalid or unsupported ivc_format              */
+  IVC_ERR_ALIGN = 3,      /* pointer not aligned to its element size        */
+  IVC_ERR_CUDA = 4,       /* a CUDA runtime call or launch failed           */
+  IVC_ERR_TIMEOUT = 5,    /* a bounded device loop ran out of iterations    */
+  IVC_ERR_NOMEM = 6,      /* workspace too small / table allocation failed  */
+  IVC_ERR_UNSUPPORTED = 7 /* combination not implemented                     */
+} ivc_status;
+
+typedef enum { IVC_AOS = 0, IVC_SOA = 1 } ivc_layout;
+/* AoS: xyz[3*i + k].  SoA: xyz[k*ld + i] (ld >= n, three rows). */
+
+typedef enum {
+  IVC_MAP_UNIFORM = 0,   /* Eq. (a_disc): n = nint(n_max psi)                 */
+  IVC_MAP_TANH = 1,      /* Sec. 2.5: n = nint(m n_max [tanh(g(2psi-1)) + c]) */
+  IVC_MAP_FRACSPLIT = 2  /* Eq. (q_split): n_p = n_phi (n_theta_max+1) + n_theta */
+} ivc_map;
+
+/* Bit layout <s,e,m>-p-t of Fig. (comp_regimes): fields from the most
+ * significant bit: [sign s][exponent e][mantissa m][n_phi p][n_theta t].
+ * n_theta_max = 2^t - 1, n_phi_max = 2^p - 1 (Sec. 2.4: the largest value
+ * the field holds).  For IVC_MAP_FRACSPLIT the p + t low bits hold
+ * n_p = n_phi (n_theta_max + 1) + n_theta with n_phi_max + 1 = nphi_max_p1
+ * and n_theta_max + 1 = floor(2^(p+t) / nphi_max_p1).
+ * Exponent field E: 0 = zero vector, 1 .. 2^e - 2 normal with
+ * r = 2^(E - exp_bias) (1 + mantissa / 2^m), 2^e - 1 = non-finite. */
+typedef struct {
+  int32_t sign_bits;      /* 0 or 1 (a stored sign bit of r, always 0)        */
+  int32_t exp_bits;       /* 2 .. 8                                           */
+  int32_t man_bits;       /* 1 .. 23; r's FP32 mantissa is truncated to this  */
+  int32_t phi_bits;       /* p                                                 */
+  int32_t theta_bits;     /* t;  s + e + m + p + t <= 64                       */
+  int32_t exp_bias;       /* b_e of Sec. 2.3 (80 for e = 7, 127 for e = 8)     */
+  int32_t map;            /* ivc_map                                           */
+  int32_t underflow_mode; /* 0: below range -> lowest value (Sec. 2.3); 1: zero word */
+  int32_t overflow_mode;  /* 0: saturate to the largest value; 1: infinite code */
+  int32_t reserved;       /* must be 0                                         */
+  double gamma;           /* IVC_MAP_TANH companding strength (paper: 0.5)     */
+  int64_t nphi_max_p1;    /* IVC_MAP_FRACSPLIT: n_phi_max + 1                  */
+} ivc_format;
+
+/* Device-side event counters (device pointer; counts are added atomically). */
+typedef struct {
+  unsigned long long n_overflow, n_underflow, n_nonfinite;
+} ivc_counts;
+
+/* Fills *f with the paper's primary layout <0,7,22>-17-18, b7 = 80
+ * (Sec. 3 and Sec. 5), uniform map, clamp below range, saturate above. */
+ivc_status ivc_format_default(ivc_format *f);
+
+/* IVC_OK if *f describes a supported format (field widths total <= 64,
+ * theta_bits <= 20, phi_bits <= 19, fractional split within 2^40). */
+ivc_status ivc_format_validate(const ivc_format *f);
+
+/* Static text for a status code. */
+const char *ivc_status_string(ivc_status s);
+
+/* Library version string. */
+const char *ivc_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Compress n FP32 3-vectors into n words (Sec. 2.1 Eq. a_disc; Sec. 2.3;
+ * Sec. 3).  xyz: device, layout per ivc_layout with leading dimension ld
+ * (ignored for AoS).  w: device, n words.  counts: optional device pointer
+ * (NULL to skip) receiving overflow / underflow / NaN counts.
+ * Each word equals the exact-arithmetic encoding of the input, except where
+ * the exact angle or magnitude lies within about 2^-40 of a rounding
+ * boundary. */
+ivc_status ivc_compress(const ivc_format *fmt, const float *xyz, ivc_layout layout,
+                        int64_t ld, int64_t n, uint64_t *w, ivc_counts *counts,
+                        ivc_stream_t stream);
+
+/* Decompress n words (Eq. a_inv, Eq. cart2sphere): x = r cos(theta) sin(phi),
+ * y = r sin(theta) sin(phi), z = r cos(phi), each component rounded away from
+ * zero to FP32 (exact zeros are +0).  Non-finite words decode to NaN (or
+ * infinities for the infinite code). */
+ivc_status ivc_decompress(const ivc_format *fmt, const uint64_t *w, int64_t n,
+                          float *xyz, ivc_layout layout, int64_t ld,
+                          ivc_stream_t stream);
+
+/* Sec. 5: c[i] = compress(decompress(a[i]) + decompress(b[i])), FP32 adds. */
+ivc_status ivc_add(const ivc_format *fmt, const uint64_t *a, const uint64_t *b,
+                   uint64_t *c, int64_t n, ivc_stream_t stream);
+
+/* y[i] = compress(fmaf(alpha, decompress(x[i]), decompress(y[i]))). */
+ivc_status ivc_axpy(const ivc_format *fmt, float alpha, const uint64_t *x,
+                    uint64_t *y, int64_t n, ivc_stream_t stream);
+
+/* Pointwise update of a compressed field (velocity v, forcing f):
+ * v_new = fmaf(dt, decompress(f[i]), decompress(v[i]));
+ * v_out[i] = compress(v_new); if rho and m_out are both non-NULL,
+ * m_out[i] = compress(rho[i] * v_new) (FP32 products).  rho: device FP32. */
+ivc_status ivc_pointwise_update(const ivc_format *fmt, float dt, const uint64_t *v,
+                                const uint64_t *f, const float *rho, uint64_t *v_out,
+                                uint64_t *m_out, int64_t n, ivc_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Uncompressed baselines (the paper's C = A + B on 3 x N FP32, Sec. 5), for
+ * the same operations on plain storage.  FP32: layout AoS or SoA (ld as
+ * above).  FP16 / BF16: AoS, elements as raw uint16_t bits; arithmetic in
+ * FP32, results rounded to nearest even. */
+ivc_status ivc_f32_add(ivc_layout layout, const float *a, const float *b, float *c,
+                       int64_t ld, int64_t n, ivc_stream_t stream);
+ivc_status ivc_f32_axpy(ivc_layout layout, float alpha, const float *x, float *y,
+                        int64_t ld, int64_t n, ivc_stream_t stream);
+
+typedef enum { IVC_F16 = 0, IVC_BF16 = 1 } ivc_half_kind;
+ivc_status ivc_half_add(ivc_half_kind kind, const uint16_t *a, const uint16_t *b,
+                        uint16_t *c, int64_t n, ivc_stream_t stream);
+ivc_status ivc_half_axpy(ivc_half_kind kind, float alpha, const uint16_t *x,
+                         uint16_t *y, int64_t n, ivc_stream_t stream);
+/* FP32 AoS <-> FP16/BF16 AoS conversion of n 3-vectors (round to nearest even). */
+ivc_status ivc_half_from_f32(ivc_half_kind kind, const float *xyz, uint16_t *h,
+                             int64_t n, ivc_stream_t stream);
+ivc_status ivc_half_to_f32(ivc_half_kind kind, const uint16_t *h, float *xyz,
+                           int64_t n, ivc_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Error statistics of stored vectors against FP32 originals (Eq. stat and the
+ * normalised errors of Sec. 3), reduced in FP64 on the device.  x, xh: device
+ * AoS FP32, n vectors; vectors with a zero or non-finite original are skipped.
+ * out: device, IVC_STATS_LEN doubles, ACCUMULATED into (zero it first):
+ *   [0] count   [1] sum e   [2] sum e^2   [3] max e
+ *   [4] sum e/|x|   [5] max e/|x|
+ *   [6] sum ang^2   [7] max ang            (angle between x and xh, radians)
+ *   [8] sum rel^2   [9] max rel            (rel = ||xh| - |x|| / |x|)
+ *   [10] count of xh non-finite where x is finite                         */
+#define IVC_STATS_LEN 11
+ivc_status ivc_error_stats(const float *x, const float *xh, int64_t n, double *out,
+                           ivc_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched form over many fields of uneven length (one persistent launch
+ * driven by a device work list, replayed from a CUDA graph). */
+typedef enum { IVC_OP_ADD = 0, IVC_OP_AXPY = 1 } ivc_op;
+
+typedef struct {
+  const uint64_t *a;  /* add: first operand;  axpy: x                 */
+  const uint64_t *b;  /* add: second operand; axpy: unused (NULL)      */
+  uint64_t *c;        /* add: result;         axpy: y (in/out)         */
+  int64_t n;          /* vectors in this field (>= 0)                  */
+  float alpha;        /* axpy scale                                    */
+  float reserved;
+} ivc_field;
+
+/* Launch shape picked by ivc_tune (or given by the caller). */
+typedef struct {
+  int32_t block;         /* threads per block (64 .. 1024, multiple of 32) */
+  int32_t vec_per_thread;/* vectors per thread per step: 1, 2 or 4          */
+  int32_t tile;          /* vectors per work-list tile (batched form)       */
+  int32_t blocks_per_sm; /* resident blocks per SM for persistent grids     */
+} ivc_launch_config;
+
+typedef struct ivc_plan_s *ivc_plan;
+
+/* Builds a plan for `nfields` fields.  The field table and the work list are
+ * written into the caller's device `workspace`; call first with
+ * workspace == NULL to get the required size in *ws_bytes.  cfg may be NULL
+ * (default shape).  The plan captures one launch (counter reset + persistent
+ * kernel) in a CUDA graph on `stream`.  The field descriptors are copied;
+ * the data pointers must stay valid while the plan is used. */
+ivc_status ivc_plan_batched(const ivc_format *fmt, ivc_op op, const ivc_field *fields,
+                            int nfields, void *workspace, size_t *ws_bytes,
+                            const ivc_launch_config *cfg, ivc_stream_t stream,
+                            ivc_plan *plan);
+/* Replays the plan's graph on `stream`. */
+ivc_status ivc_launch_plan(ivc_plan plan, ivc_stream_t stream);
+/* Same work as ivc_launch_plan, as one ordinary persistent launch (no graph). */
+ivc_status ivc_launch_plan_direct(ivc_plan plan, ivc_stream_t stream);
+/* Device status word of the plan's last launch: IVC_OK, or IVC_ERR_TIMEOUT
+ * if the bounded scheduling loop ran out.  Synchronises `stream`. */
+ivc_status ivc_plan_status(ivc_plan plan, ivc_stream_t stream);
+ivc_status ivc_plan_destroy(ivc_plan plan);
+
+/* Times candidate launch shapes of `op` on the caller's buffers (n vectors;
+ * for IVC_OP_AXPY, b is used as the y operand and is overwritten; for
+ * IVC_OP_ADD, c is overwritten) and writes the fastest to *best.  Runs
+ * synchronously on `stream`. */
+ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const uint64_t *b,
+                    uint64_t *c, int64_t n, ivc_stream_t stream, ivc_launch_config *best);
+
+/* Add with an explicit launch shape (cfg NULL = default). */
+ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t *b,
+                       uint64_t *c, int64_t n, const ivc_launch_config *cfg,
+                       ivc_stream_t stream);
+
+/* Frees the cached per-format tables on the current device. */
+ivc_status ivc_release_tables(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IVC_H */

@@ -1,0 +1,618 @@
+// C ABI of the compressed-vector library: argument checks, format set-up,
+// per-format trigonometric tables, launch shapes, batched plans and the
+// launch-shape tuner.  Kernels live in ivc_ops.cu and ivc_baseline.cu.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "ivc_internal.h"
+
+using namespace ivc;
+
+namespace {
+
+const long double kPiL = 3.14159265358979323846264338327950288419716939937510L;
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// ------------------------------------------------------------ format set-up
+
+struct Geometry {
+  int N, M;
+};
+
+ivc_status geometry(const ivc_format *f, Geometry *g) {
+  if (!f) return IVC_ERR_ARG;
+  const int total = f->sign_bits + f->exp_bits + f->man_bits + f->phi_bits + f->theta_bits;
+  if (f->sign_bits < 0 || f->sign_bits > 1 || f->exp_bits < 2 || f->exp_bits > 8 ||
+      f->man_bits < 1 || f->man_bits > 23 || f->phi_bits < 1 || f->theta_bits < 1 ||
+      total > 64 || f->reserved != 0 || f->underflow_mode < 0 || f->underflow_mode > 1 ||
+      f->overflow_mode < 0 || f->overflow_mode > 1)
+    return IVC_ERR_FORMAT;
+  // every normal exponent field must map to a normal FP32 exponent
+  const int emaxn = (1 << f->exp_bits) - 2;
+  const int e_off = f->exp_bias - 127;
+  if (1 - e_off < 1 || emaxn - e_off > 254) return IVC_ERR_FORMAT;
+  long long N, M;
+  if (f->map == IVC_MAP_FRACSPLIT) {
+    const int P = f->phi_bits + f->theta_bits;
+    if (P > 40 || f->nphi_max_p1 < 2) return IVC_ERR_FORMAT;
+    M = f->nphi_max_p1 - 1;
+    N = ((long long)1 << P) / f->nphi_max_p1 - 1;
+  } else if (f->map == IVC_MAP_UNIFORM || f->map == IVC_MAP_TANH) {
+    if (f->theta_bits > 19 || f->phi_bits > 18) return IVC_ERR_FORMAT;
+    N = (1LL << f->theta_bits) - 1;
+    M = (1LL << f->phi_bits) - 1;
+    if (f->map == IVC_MAP_TANH && !(f->gamma > 0.0 && f->gamma < 20.0)) return IVC_ERR_FORMAT;
+  } else {
+    return IVC_ERR_FORMAT;
+  }
+  if (N < 1 || M < 1 || N >= (1LL << 19) || M >= (1LL << 18)) return IVC_ERR_FORMAT;
+  g->N = (int)N;
+  g->M = (int)M;
+  return IVC_OK;
+}
+
+void ff_split(long double v, float &h, float &l) {
+  h = (float)v;
+  l = (float)(v - (long double)h);
+}
+
+TabEntry entry_of(long double c, long double s) {
+  TabEntry e;
+  ff_split(c, e.ch, e.cl);
+  ff_split(s, e.sh, e.sl);
+  return e;
+}
+
+// Head table of the folded grid pi b / (2D): entries at b = 256 i.
+void uniform_table(int D, std::vector<TabEntry> &out) {
+  const int nent = ((D / 2) >> 8) + 1;
+  for (int i = 0; i < nent; ++i) {
+    if (i == 0) {
+      out.push_back(TabEntry{1.0f, 0.0f, 0.0f, 0.0f});
+      continue;
+    }
+    const long double a = kPiL * (256.0L * i) / (2.0L * D);
+    out.push_back(entry_of(cosl(a), sinl(a)));
+  }
+}
+
+// tanh companding (Sec. 2.5): psi^ of code n and psi at boundary t.
+long double psi_of_t(long double t, long double nmax, long double g) {
+  const long double c = tanhl(g);
+  return 0.5L * (1.0L + atanhl(c * (2.0L * t / nmax - 1.0L)) / g);
+}
+
+TabEntry theta_entry_psi(long double psi) {  // theta = pi (2 psi - 1)
+  if (psi == 0.5L) return TabEntry{1.0f, 0.0f, 0.0f, 0.0f};
+  if (psi == 0.0L || psi == 1.0L) return TabEntry{-1.0f, 0.0f, 0.0f, 0.0f};
+  const long double th = kPiL * (2.0L * psi - 1.0L);
+  return entry_of(cosl(th), sinl(th));
+}
+
+TabEntry phi_entry_psi(long double psi) {  // phi = pi psi
+  if (psi == 0.0L) return TabEntry{1.0f, 0.0f, 0.0f, 0.0f};
+  if (psi == 1.0L) return TabEntry{-1.0f, 0.0f, 0.0f, 0.0f};
+  if (psi == 0.5L) return TabEntry{0.0f, 0.0f, 1.0f, 0.0f};
+  const long double ph = kPiL * psi;
+  return entry_of(cosl(ph), sinl(ph));
+}
+
+struct TableKey {
+  int device, map, N, M;
+  double gamma;
+  bool operator<(const TableKey &o) const {
+    return std::tie(device, map, N, M, gamma) < std::tie(o.device, o.map, o.N, o.M, o.gamma);
+  }
+};
+
+struct TableSet {
+  TabEntry *dev = nullptr;
+  size_t n_uniform_t = 0, n_uniform_p = 0;
+  size_t off_dec_t = 0, off_dec_p = 0, off_bnd_t = 0, off_bnd_p = 0;
+};
+
+std::mutex g_mu;
+std::map<TableKey, TableSet> g_tables;
+
+ivc_status get_tables(const ivc_format *f, const Geometry &g, int device, TableSet *out) {
+  TableKey key{device, f->map, g.N, g.M, f->map == IVC_MAP_TANH ? f->gamma : 0.0};
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_tables.find(key);
+  if (it != g_tables.end()) {
+    *out = it->second;
+    return IVC_OK;
+  }
+  std::vector<TabEntry> host;
+  TableSet ts;
+  if (f->map == IVC_MAP_TANH) {
+    const long double gm = (long double)f->gamma;
+    ts.off_dec_t = host.size();
+    for (int n = 0; n <= g.N; ++n) {
+      long double psi = (n == 0) ? 0.0L : (n == g.N) ? 1.0L : (2LL * n == g.N) ? 0.5L
+                        : psi_of_t((long double)n, (long double)g.N, gm);
+      host.push_back(theta_entry_psi(psi));
+    }
+    ts.off_dec_p = host.size();
+    for (int n = 0; n <= g.M; ++n) {
+      long double psi = (n == 0) ? 0.0L : (n == g.M) ? 1.0L : (2LL * n == g.M) ? 0.5L
+                        : psi_of_t((long double)n, (long double)g.M, gm);
+      host.push_back(phi_entry_psi(psi));
+    }
+    ts.off_bnd_t = host.size();
+    for (int k = 0; k < g.N; ++k) {
+      long double psi = (2LL * k + 1 == g.N) ? 0.5L
+                        : psi_of_t((long double)k + 0.5L, (long double)g.N, gm);
+      host.push_back(theta_entry_psi(psi));
+    }
+    ts.off_bnd_p = host.size();
+    for (int k = 0; k < g.M; ++k) {
+      long double psi = (2LL * k + 1 == g.M) ? 0.5L
+                        : psi_of_t((long double)k + 0.5L, (long double)g.M, gm);
+      host.push_back(phi_entry_psi(psi));
+    }
+  } else {
+    uniform_table(g.N, host);
+    ts.n_uniform_t = host.size();
+    uniform_table(2 * g.M, host);
+    ts.n_uniform_p = host.size() - ts.n_uniform_t;
+  }
+  void *d = nullptr;
+  if (cudaMalloc(&d, host.size() * sizeof(TabEntry)) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_NOMEM;
+  }
+  if (cudaMemcpy(d, host.data(), host.size() * sizeof(TabEntry), cudaMemcpyHostToDevice) !=
+      cudaSuccess) {
+    cudaFree(d);
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  ts.dev = static_cast<TabEntry *>(d);
+  g_tables[key] = ts;
+  *out = ts;
+  return IVC_OK;
+}
+
+ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
+  Geometry g;
+  ivc_status st = geometry(f, &g);
+  if (st != IVC_OK) return st;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  TableSet ts;
+  st = get_tables(f, g, dev, &ts);
+  if (st != IVC_OK) return st;
+  std::memset(F, 0, sizeof(*F));
+  F->sh_phi = (uint32_t)f->theta_bits;
+  F->sh_m = (uint32_t)(f->theta_bits + f->phi_bits);
+  F->sh_e = F->sh_m + (uint32_t)f->man_bits;
+  F->mask_e = (1u << f->exp_bits) - 1u;
+  F->mask_m = (1u << f->man_bits) - 1u;
+  F->mask_phi = (1u << f->phi_bits) - 1u;
+  F->mask_theta = (1u << f->theta_bits) - 1u;
+  F->m_shift = (uint32_t)(23 - f->man_bits);
+  const int P = f->phi_bits + f->theta_bits;
+  F->mask_np = (P >= 64) ? ~0ull : ((1ull << P) - 1ull);
+  F->e_off = f->exp_bias - 127;
+  F->e_maxn = (1 << f->exp_bits) - 2;
+  F->e_all = (1 << f->exp_bits) - 1;
+  F->N = g.N;
+  F->M = g.M;
+  F->under_mode = f->underflow_mode;
+  F->over_mode = f->overflow_mode;
+  F->tscale_t = (float)((long double)g.N / (2.0L * kPiL));
+  F->thalf_t = (float)(0.5L * g.N);
+  F->tmax_t = (float)g.N - 0.25f;
+  F->tscale_p = (float)((long double)g.M / kPiL);
+  F->tmax_p = (float)g.M - 0.25f;
+  F->Dt = g.N;
+  F->Dp = 2 * g.M;
+  F->nent_t = ((F->Dt / 2) >> 8) + 1;
+  F->nent_p = ((F->Dp / 2) >> 8) + 1;
+  ff_split(kPiL / (2.0L * F->Dt), F->Kt_h, F->Kt_l);
+  ff_split(kPiL / (2.0L * F->Dp), F->Kp_h, F->Kp_l);
+  F->tab = ts.dev;
+  {
+    const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+    const unsigned __int128 d = (unsigned __int128)(g.N + 1);
+    F->div_magic = (uint64_t)((two64 + d - 1) / d);
+  }
+  if (f->map == IVC_MAP_TANH) {
+    F->gam = (float)f->gamma;
+    F->tanh_c = (float)tanhl((long double)f->gamma);
+    F->tanh_inv2c = (float)(1.0L / (2.0L * tanhl((long double)f->gamma)));
+    F->dec_t = ts.dev + ts.off_dec_t;
+    F->dec_p = ts.dev + ts.off_dec_p;
+    F->bnd_t = ts.dev + ts.off_bnd_t;
+    F->bnd_p = ts.dev + ts.off_bnd_p;
+    F->nent_t = F->nent_p = 0;
+  }
+  *map_out = f->map;
+  return IVC_OK;
+}
+
+// ------------------------------------------------------------ launch shapes
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+LaunchShape default_shape(int map, int kind, const DevFormat &F, int64_t n, int vec2,
+                          const ivc_launch_config *cfg) {
+  LaunchShape s;
+  s.block = (cfg && cfg->block > 0) ? cfg->block : 256;
+  if (s.block > 256) s.block = 256;
+  s.vec2 = vec2;
+  s.smem = table_smem_bytes(F, map);
+  int bps = (cfg && cfg->blocks_per_sm > 0) ? cfg->blocks_per_sm : 0;
+  const int occ = occupancy(map, kind, s.block, s.smem);
+  if (bps <= 0 || (occ > 0 && bps > occ)) bps = occ > 0 ? occ : 1;
+  const int64_t per_block = (int64_t)s.block * (vec2 ? 2 : 1);
+  const int64_t need = (n + per_block - 1) / per_block;
+  int64_t grid = (int64_t)sm_count() * bps;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  s.grid = (int)grid;
+  return s;
+}
+
+ivc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return IVC_OK;
+  return IVC_ERR_CUDA;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char *ivc_status_string(ivc_status s) {
+  switch (s) {
+    case IVC_OK: return "ok";
+    case IVC_ERR_ARG: return "invalid argument";
+    case IVC_ERR_FORMAT: return "invalid or unsupported format";
+    case IVC_ERR_ALIGN: return "misaligned pointer";
+    case IVC_ERR_CUDA: return "CUDA runtime error";
+    case IVC_ERR_TIMEOUT: return "bounded device loop ran out";
+    case IVC_ERR_NOMEM: return "out of memory or workspace too small";
+    case IVC_ERR_UNSUPPORTED: return "unsupported combination";
+  }
+  return "unknown status";
+}
+
+const char *ivc_version(void) { return "ivc 0.1 (sm_103a)"; }
+
+ivc_status ivc_format_default(ivc_format *f) {
+  if (!f) return IVC_ERR_ARG;
+  std::memset(f, 0, sizeof(*f));
+  f->sign_bits = 0;
+  f->exp_bits = 7;
+  f->man_bits = 22;
+  f->phi_bits = 17;
+  f->theta_bits = 18;
+  f->exp_bias = 80;
+  f->map = IVC_MAP_UNIFORM;
+  f->gamma = 0.5;
+  return IVC_OK;
+}
+
+ivc_status ivc_format_validate(const ivc_format *f) {
+  Geometry g;
+  return geometry(f, &g);
+}
+
+ivc_status ivc_release_tables(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto it = g_tables.begin(); it != g_tables.end();) {
+    if (it->first.device == dev) {
+      cudaFree(it->second.dev);
+      it = g_tables.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return IVC_OK;
+}
+
+ivc_status ivc_compress(const ivc_format *fmt, const float *xyz, ivc_layout layout, int64_t ld,
+                        int64_t n, uint64_t *w, ivc_counts *counts, ivc_stream_t stream) {
+  if (n < 0 || (layout != IVC_AOS && layout != IVC_SOA)) return IVC_ERR_ARG;
+  if (layout == IVC_SOA && ld < n) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!xyz || !w) return IVC_ERR_ARG;
+  if (!aligned(xyz, 4) || !aligned(w, 8) || (counts && !aligned(counts, 8))) return IVC_ERR_ALIGN;
+  const LaunchShape s = default_shape(map, K_COMPRESS, F, n, 0, nullptr);
+  return cuda_status(launch_compress(map, F, xyz, layout, ld, n, w, counts, s, stream));
+}
+
+ivc_status ivc_decompress(const ivc_format *fmt, const uint64_t *w, int64_t n, float *xyz,
+                          ivc_layout layout, int64_t ld, ivc_stream_t stream) {
+  if (n < 0 || (layout != IVC_AOS && layout != IVC_SOA)) return IVC_ERR_ARG;
+  if (layout == IVC_SOA && ld < n) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!xyz || !w) return IVC_ERR_ARG;
+  if (!aligned(xyz, 4) || !aligned(w, 8)) return IVC_ERR_ALIGN;
+  const LaunchShape s = default_shape(map, K_DECOMPRESS, F, n, 0, nullptr);
+  return cuda_status(launch_decompress(map, F, w, n, xyz, layout, ld, s, stream));
+}
+
+ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t *b, uint64_t *c,
+                       int64_t n, const ivc_launch_config *cfg, ivc_stream_t stream) {
+  if (n < 0) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!a || !b || !c) return IVC_ERR_ARG;
+  if (!aligned(a, 8) || !aligned(b, 8) || !aligned(c, 8)) return IVC_ERR_ALIGN;
+  const int vec2 = (aligned(a, 16) && aligned(b, 16) && aligned(c, 16) &&
+                    !(cfg && cfg->vec_per_thread == 1)) ? 1 : 0;
+  const LaunchShape s = default_shape(map, K_ADD, F, n, vec2, cfg);
+  return cuda_status(launch_add(map, F, a, b, c, n, s, stream));
+}
+
+ivc_status ivc_add(const ivc_format *fmt, const uint64_t *a, const uint64_t *b, uint64_t *c,
+                   int64_t n, ivc_stream_t stream) {
+  return ivc_add_cfg(fmt, a, b, c, n, nullptr, stream);
+}
+
+ivc_status ivc_axpy(const ivc_format *fmt, float alpha, const uint64_t *x, uint64_t *y, int64_t n,
+                    ivc_stream_t stream) {
+  if (n < 0) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!x || !y) return IVC_ERR_ARG;
+  if (!aligned(x, 8) || !aligned(y, 8)) return IVC_ERR_ALIGN;
+  const int vec2 = (aligned(x, 16) && aligned(y, 16)) ? 1 : 0;
+  const LaunchShape s = default_shape(map, K_AXPY, F, n, vec2, nullptr);
+  return cuda_status(launch_axpy(map, F, alpha, x, y, n, s, stream));
+}
+
+ivc_status ivc_pointwise_update(const ivc_format *fmt, float dt, const uint64_t *v,
+                                const uint64_t *f, const float *rho, uint64_t *v_out,
+                                uint64_t *m_out, int64_t n, ivc_stream_t stream) {
+  if (n < 0) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!v || !f || !v_out) return IVC_ERR_ARG;
+  if (!aligned(v, 8) || !aligned(f, 8) || !aligned(v_out, 8) || (m_out && !aligned(m_out, 8)) ||
+      (rho && !aligned(rho, 4)))
+    return IVC_ERR_ALIGN;
+  const LaunchShape s = default_shape(map, K_UPDATE, F, n, 0, nullptr);
+  return cuda_status(launch_update(map, F, dt, v, f, rho, v_out, m_out, n, s, stream));
+}
+
+// ------------------------------------------------------------------ batched
+
+struct ivc_plan_s {
+  int device = 0;
+  int map = 0;
+  int op = 0;
+  DevFormat F{};
+  PlanDev P{};
+  LaunchShape shape{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static size_t plan_ws_bytes(int nfields) {
+  size_t b = round_up(sizeof(FieldDesc) * (size_t)nfields, 256);
+  b += round_up(sizeof(int64_t) * (size_t)(nfields + 1), 256);
+  b += 256;  // counter + status
+  return b;
+}
+
+ivc_status ivc_plan_batched(const ivc_format *fmt, ivc_op op, const ivc_field *fields,
+                            int nfields, void *workspace, size_t *ws_bytes,
+                            const ivc_launch_config *cfg, ivc_stream_t stream, ivc_plan *plan) {
+  if (!ws_bytes || nfields < 1 || (op != IVC_OP_ADD && op != IVC_OP_AXPY)) return IVC_ERR_ARG;
+  const size_t need = plan_ws_bytes(nfields);
+  if (!workspace) {
+    *ws_bytes = need;
+    return IVC_OK;
+  }
+  if (!fields || !plan) return IVC_ERR_ARG;
+  if (*ws_bytes < need) return IVC_ERR_NOMEM;
+  if (!aligned(workspace, 256)) return IVC_ERR_ALIGN;
+  int64_t total_n = 0;
+  for (int i = 0; i < nfields; ++i) {
+    const ivc_field &f = fields[i];
+    if (f.n < 0) return IVC_ERR_ARG;
+    if (f.n > 0 && (!f.a || !f.c || (op == IVC_OP_ADD && !f.b))) return IVC_ERR_ARG;
+    if (!aligned(f.a, 8) || !aligned(f.c, 8) || (f.b && !aligned(f.b, 8))) return IVC_ERR_ALIGN;
+    total_n += f.n;
+  }
+  ivc_plan_s *p = new ivc_plan_s();
+  ivc_status st = make_devformat(fmt, &p->F, &p->map);
+  if (st != IVC_OK) {
+    delete p;
+    return st;
+  }
+  p->op = op;
+  cudaGetDevice(&p->device);
+  const int tile = (cfg && cfg->tile > 0) ? cfg->tile : 8192;
+  char *ws = static_cast<char *>(workspace);
+  FieldDesc *d_fields = reinterpret_cast<FieldDesc *>(ws);
+  ws += round_up(sizeof(FieldDesc) * (size_t)nfields, 256);
+  int64_t *d_tiles = reinterpret_cast<int64_t *>(ws);
+  ws += round_up(sizeof(int64_t) * (size_t)(nfields + 1), 256);
+  unsigned long long *d_counter = reinterpret_cast<unsigned long long *>(ws);
+  int *d_status = reinterpret_cast<int *>(ws + 64);
+
+  std::vector<FieldDesc> h(nfields);
+  int64_t total_tiles = 0;
+  for (int i = 0; i < nfields; ++i) {
+    h[i] = FieldDesc{fields[i].a, op == IVC_OP_ADD ? fields[i].b : nullptr, fields[i].c,
+                     fields[i].n, fields[i].alpha, 0.0f};
+    total_tiles += (fields[i].n + tile - 1) / tile;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_fields, h.data(), sizeof(FieldDesc) * nfields,
+                                  cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = launch_tile_scan(d_fields, nfields, tile, d_tiles, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int), stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // host copy source must outlive it
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return IVC_ERR_CUDA;
+  }
+  p->P = PlanDev{d_fields, d_tiles, d_counter, d_status, total_tiles, nfields, tile};
+  const int kind = op == IVC_OP_ADD ? K_BATCH_ADD : K_BATCH_AXPY;
+  LaunchShape s;
+  s.block = (cfg && cfg->block > 0 && cfg->block <= 256) ? cfg->block : 256;
+  s.vec2 = 1;
+  s.smem = table_smem_bytes(p->F, p->map);
+  const int occ = occupancy(p->map, kind, s.block, s.smem);
+  int bps = (cfg && cfg->blocks_per_sm > 0) ? cfg->blocks_per_sm : occ;
+  if (occ > 0 && bps > occ) bps = occ;
+  if (bps < 1) bps = 1;
+  int64_t grid = (int64_t)sm_count() * bps;
+  if (grid > total_tiles) grid = total_tiles > 0 ? total_tiles : 1;
+  s.grid = (int)grid;
+  p->shape = s;
+  (void)total_n;
+
+  // Capture counter reset + persistent launch into a graph on a private stream.
+  cudaStream_t cap = nullptr;
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), cap);
+    cudaError_t e2 = e1 == cudaSuccess ? launch_batched(p->map, op, p->F, p->P, s, cap) : e1;
+    cudaError_t e3 = cudaStreamEndCapture(cap, &p->graph);
+    e = e2 != cudaSuccess ? e2 : e3;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (cap) cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    delete p;
+    return IVC_ERR_CUDA;
+  }
+  *plan = p;
+  return IVC_OK;
+}
+
+ivc_status ivc_launch_plan(ivc_plan plan, ivc_stream_t stream) {
+  if (!plan || !plan->exec) return IVC_ERR_ARG;
+  return cuda_status(cudaGraphLaunch(plan->exec, stream));
+}
+
+ivc_status ivc_launch_plan_direct(ivc_plan plan, ivc_stream_t stream) {
+  if (!plan) return IVC_ERR_ARG;
+  cudaError_t e = cudaMemsetAsync(plan->P.counter, 0, sizeof(unsigned long long), stream);
+  if (e == cudaSuccess) e = launch_batched(plan->map, plan->op, plan->F, plan->P, plan->shape, stream);
+  return cuda_status(e);
+}
+
+ivc_status ivc_plan_status(ivc_plan plan, ivc_stream_t stream) {
+  if (!plan) return IVC_ERR_ARG;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, plan->P.status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return IVC_ERR_CUDA;
+  return (ivc_status)h;
+}
+
+ivc_status ivc_plan_destroy(ivc_plan plan) {
+  if (!plan) return IVC_ERR_ARG;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  delete plan;
+  return IVC_OK;
+}
+
+// ------------------------------------------------------------------ tuner
+
+ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const uint64_t *b,
+                    uint64_t *c, int64_t n, ivc_stream_t stream, ivc_launch_config *best) {
+  if (!best || n <= 0 || !a || !b || (op == IVC_OP_ADD && !c)) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  const int kind = op == IVC_OP_ADD ? K_ADD : K_AXPY;
+  const int vec2 = (aligned(a, 16) && aligned(b, 16) && (!c || aligned(c, 16))) ? 1 : 0;
+  const int blocks[] = {64, 128, 256};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  float best_ms = 1e30f;
+  ivc_launch_config bc{256, vec2 ? 2 : 1, 8192, 0};
+  for (int blk : blocks) {
+    const size_t smem = table_smem_bytes(F, map);
+    const int occ = occupancy(map, kind, blk, smem);
+    for (int bps = 1; bps <= occ; bps *= 2) {
+      ivc_launch_config cfg{blk, vec2 ? 2 : 1, 8192, bps};
+      LaunchShape s = default_shape(map, kind, F, n, vec2, &cfg);
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, stream);
+        cudaError_t e = op == IVC_OP_ADD ? launch_add(map, F, a, b, c, n, s, stream)
+                                         : launch_axpy(map, F, 0.7f, a, const_cast<uint64_t *>(b),
+                                                       n, s, stream);
+        cudaEventRecord(e1, stream);
+        if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaGetLastError();
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return IVC_ERR_CUDA;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < ms_min) ms_min = ms;
+      }
+      if (ms_min < best_ms) {
+        best_ms = ms_min;
+        bc = cfg;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best = bc;
+  return IVC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Internal interface between the C ABI layer (ivc_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ivc.h"
+#include "ivc_device.cuh"
+
+namespace ivc {
+
+enum KernelKind : int {
+  K_COMPRESS = 0,
+  K_DECOMPRESS = 1,
+  K_ADD = 2,
+  K_AXPY = 3,
+  K_UPDATE = 4,
+  K_BATCH_ADD = 5,
+  K_BATCH_AXPY = 6,
+};
+
+struct LaunchShape {
+  int block;   // threads per block
+  int grid;    // blocks
+  int vec2;    // 1: two words per 16-byte access where aligned
+  size_t smem; // dynamic shared memory (tables)
+};
+
+// One field of a batched launch (device copy of ivc_field).
+struct FieldDesc {
+  const uint64_t *a;
+  const uint64_t *b;
+  uint64_t *c;
+  int64_t n;
+  float alpha;
+  float pad;
+};
+
+// Device view of a batched plan.
+struct PlanDev {
+  const FieldDesc *fields;
+  const int64_t *tile_start;  // nfields + 1 prefix sums of tiles per field
+  unsigned long long *counter;
+  int *status;
+  int64_t total_tiles;
+  int nfields;
+  int tile;
+};
+
+size_t table_smem_bytes(const DevFormat &F, int map);
+
+cudaError_t launch_compress(int map, const DevFormat &F, const float *xyz, int layout, int64_t ld,
+                            int64_t n, uint64_t *w, ivc_counts *counts, const LaunchShape &s,
+                            cudaStream_t st);
+cudaError_t launch_decompress(int map, const DevFormat &F, const uint64_t *w, int64_t n,
+                              float *xyz, int layout, int64_t ld, const LaunchShape &s,
+                              cudaStream_t st);
+cudaError_t launch_add(int map, const DevFormat &F, const uint64_t *a, const uint64_t *b,
+                       uint64_t *c, int64_t n, const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_axpy(int map, const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
+                        int64_t n, const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t *v,
+                          const uint64_t *f, const float *rho, uint64_t *v_out, uint64_t *m_out,
+                          int64_t n, const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P,
+                           const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,
+                             cudaStream_t st);
+
+// Resident blocks per SM of a kernel at a block size (0 if it cannot run).
+int occupancy(int map, int kind, int block, size_t smem);
+
+}  // namespace ivc

@@ -1,0 +1,339 @@
+// Compressed-vector kernels: compress, decompress, and the fused
+// decompress -> FP32 op -> recompress kernels (Sec. 5: C = A + B), single-field
+// and batched (persistent, work-list driven).
+//
+// Memory access: words move as 16-byte pairs (ulonglong2) with streaming
+// cache hints when the pointers are 16-byte aligned; the trigonometric head
+// tables of the uniform grids are staged once per block into shared memory.
+// Grids are persistent-style grid-stride loops sized from the SM count.
+#include "ivc_internal.h"
+
+namespace ivc {
+
+#define IVC_TABLES(F, MAP)                                        \
+  extern __shared__ TabEntry ivc_smem_tab[];                      \
+  stage_tables<MAP>(F, ivc_smem_tab);                             \
+  const TabEntry *tab_t = ivc_smem_tab;                           \
+  const TabEntry *tab_p = ivc_smem_tab + (MAP == MAP_TANH ? 0 : F.nent_t)
+
+__device__ __forceinline__ void flush_counts(uint32_t flags, ivc_counts *counts) {
+  if (counts == nullptr) return;
+  const unsigned m = __activemask();
+  const int lead = __ffs(m) - 1;
+  const unsigned o = __popc(__ballot_sync(m, flags & 1u));
+  const unsigned u = __popc(__ballot_sync(m, flags & 2u));
+  const unsigned q = __popc(__ballot_sync(m, flags & 4u));
+  if ((int)(threadIdx.x & 31) == lead) {
+    if (o) atomicAdd(&counts->n_overflow, (unsigned long long)o);
+    if (u) atomicAdd(&counts->n_underflow, (unsigned long long)u);
+    if (q) atomicAdd(&counts->n_nonfinite, (unsigned long long)q);
+  }
+}
+
+// ------------------------------------------------------------------ compress
+
+template <int MAP>
+__global__ void __launch_bounds__(256) k_compress(const __grid_constant__ DevFormat F,
+                                                  const float *__restrict__ xyz, int layout,
+                                                  int64_t ld, int64_t n, uint64_t *w,
+                                                  ivc_counts *counts) {
+  IVC_TABLES(F, MAP);
+  uint32_t flags = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    float x, y, z;
+    if (layout == IVC_AOS) {
+      x = __ldcs(xyz + 3 * i);
+      y = __ldcs(xyz + 3 * i + 1);
+      z = __ldcs(xyz + 3 * i + 2);
+    } else {
+      x = __ldcs(xyz + i);
+      y = __ldcs(xyz + ld + i);
+      z = __ldcs(xyz + 2 * ld + i);
+    }
+    __stcs(reinterpret_cast<unsigned long long *>(w) + i,
+           (unsigned long long)encode_vec<MAP>(x, y, z, F, tab_t, tab_p, flags));
+  }
+  flush_counts(flags, counts);
+}
+
+// ---------------------------------------------------------------- decompress
+
+template <int MAP>
+__global__ void __launch_bounds__(256) k_decompress(const __grid_constant__ DevFormat F,
+                                                    const uint64_t *__restrict__ w, int64_t n,
+                                                    float *xyz, int layout, int64_t ld) {
+  IVC_TABLES(F, MAP);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t word = __ldcs(reinterpret_cast<const unsigned long long *>(w) + i);
+    const float3 v = decode_word<MAP>(word, F, tab_t, tab_p);
+    if (layout == IVC_AOS) {
+      __stcs(xyz + 3 * i, v.x);
+      __stcs(xyz + 3 * i + 1, v.y);
+      __stcs(xyz + 3 * i + 2, v.z);
+    } else {
+      __stcs(xyz + i, v.x);
+      __stcs(xyz + ld + i, v.y);
+      __stcs(xyz + 2 * ld + i, v.z);
+    }
+  }
+}
+
+// ------------------------------------------------------------- fused kernels
+
+struct OpAdd {
+  __device__ __forceinline__ float3 operator()(float3 a, float3 b) const {
+    return make_float3(a.x + b.x, a.y + b.y, a.z + b.z);
+  }
+};
+
+struct OpAxpy {  // fmaf(alpha, x, y)
+  float alpha;
+  __device__ __forceinline__ float3 operator()(float3 x, float3 y) const {
+    return make_float3(fmaf(alpha, x.x, y.x), fmaf(alpha, x.y, y.y), fmaf(alpha, x.z, y.z));
+  }
+};
+
+template <int MAP, class Op>
+__device__ __forceinline__ uint64_t fused1(uint64_t wa, uint64_t wb, const Op &op,
+                                           const DevFormat &F, const TabEntry *tab_t,
+                                           const TabEntry *tab_p, uint32_t &flags) {
+  const float3 u = decode_word<MAP>(wa, F, tab_t, tab_p);
+  const float3 v = decode_word<MAP>(wb, F, tab_t, tab_p);
+  const float3 s = op(u, v);
+  return encode_vec<MAP>(s.x, s.y, s.z, F, tab_t, tab_p, flags);
+}
+
+// out[i] = encode(op(decode(a[i]), decode(b[i]))) over [0, n) with the
+// calling block set (grid-stride over `nthreads` threads starting at `tid`).
+template <int MAP, class Op>
+__device__ __forceinline__ void fused_range(const uint64_t *a, const uint64_t *b, uint64_t *out,
+                                            int64_t n, bool vec2, int64_t tid, int64_t nthreads,
+                                            const Op &op, const DevFormat &F,
+                                            const TabEntry *tab_t, const TabEntry *tab_p,
+                                            uint32_t &flags) {
+  if (vec2) {
+    const int64_t n2 = n >> 1;
+    const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(a);
+    const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(b);
+    ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(out);
+    for (int64_t i = tid; i < n2; i += nthreads) {
+      const ulonglong2 wa = __ldcs(a2 + i);
+      const ulonglong2 wb = __ldcs(b2 + i);
+      ulonglong2 r;
+      r.x = fused1<MAP>(wa.x, wb.x, op, F, tab_t, tab_p, flags);
+      r.y = fused1<MAP>(wa.y, wb.y, op, F, tab_t, tab_p, flags);
+      __stcs(o2 + i, r);
+    }
+    if ((n & 1) && tid == 0) {
+      const int64_t i = n - 1;
+      out[i] = fused1<MAP>(a[i], b[i], op, F, tab_t, tab_p, flags);
+    }
+  } else {
+    for (int64_t i = tid; i < n; i += nthreads) {
+      const uint64_t wa = __ldcs(reinterpret_cast<const unsigned long long *>(a) + i);
+      const uint64_t wb = __ldcs(reinterpret_cast<const unsigned long long *>(b) + i);
+      __stcs(reinterpret_cast<unsigned long long *>(out) + i,
+             (unsigned long long)fused1<MAP>(wa, wb, op, F, tab_t, tab_p, flags));
+    }
+  }
+}
+
+template <int MAP>
+__global__ void __launch_bounds__(256) k_add(const __grid_constant__ DevFormat F,
+                                             const uint64_t *a, const uint64_t *b, uint64_t *c,
+                                             int64_t n, int vec2) {
+  IVC_TABLES(F, MAP);
+  uint32_t flags = 0;
+  fused_range<MAP>(a, b, c, n, vec2 != 0, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                   (int64_t)gridDim.x * blockDim.x, OpAdd{}, F, tab_t, tab_p, flags);
+}
+
+template <int MAP>
+__global__ void __launch_bounds__(256) k_axpy(const __grid_constant__ DevFormat F, float alpha,
+                                              const uint64_t *x, uint64_t *y, int64_t n,
+                                              int vec2) {
+  IVC_TABLES(F, MAP);
+  uint32_t flags = 0;
+  fused_range<MAP>(x, y, y, n, vec2 != 0, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                   (int64_t)gridDim.x * blockDim.x, OpAxpy{alpha}, F, tab_t, tab_p, flags);
+}
+
+// v_out = encode(fmaf(dt, decode(f), decode(v))); m_out = encode(rho * v_new).
+template <int MAP>
+__global__ void __launch_bounds__(256) k_update(const __grid_constant__ DevFormat F, float dt,
+                                                const uint64_t *v, const uint64_t *f,
+                                                const float *__restrict__ rho, uint64_t *v_out,
+                                                uint64_t *m_out, int64_t n) {
+  IVC_TABLES(F, MAP);
+  uint32_t flags = 0;
+  const bool want_m = (rho != nullptr) && (m_out != nullptr);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float3 vv = decode_word<MAP>(__ldcs(reinterpret_cast<const unsigned long long *>(v) + i),
+                                       F, tab_t, tab_p);
+    const float3 ff = decode_word<MAP>(__ldcs(reinterpret_cast<const unsigned long long *>(f) + i),
+                                       F, tab_t, tab_p);
+    const float3 s = make_float3(fmaf(dt, ff.x, vv.x), fmaf(dt, ff.y, vv.y), fmaf(dt, ff.z, vv.z));
+    __stcs(reinterpret_cast<unsigned long long *>(v_out) + i,
+           (unsigned long long)encode_vec<MAP>(s.x, s.y, s.z, F, tab_t, tab_p, flags));
+    if (want_m) {
+      const float q = __ldcs(rho + i);
+      __stcs(reinterpret_cast<unsigned long long *>(m_out) + i,
+             (unsigned long long)encode_vec<MAP>(q * s.x, q * s.y, q * s.z, F, tab_t, tab_p,
+                                                 flags));
+    }
+  }
+}
+
+// ------------------------------------------------------------------- batched
+
+// Persistent kernel: blocks pull tiles from a device counter; the loop is
+// bounded by the tile count (every pull advances the counter), and reports
+// IVC_ERR_TIMEOUT in the plan status if the bound is ever reached.
+template <int MAP, int OP>
+__global__ void __launch_bounds__(256) k_batched(const __grid_constant__ DevFormat F,
+                                                 const __grid_constant__ PlanDev P) {
+  IVC_TABLES(F, MAP);
+  __shared__ long long s_tile;
+  uint32_t flags = 0;
+  bool done = false;
+  for (int64_t iter = 0; iter <= P.total_tiles; ++iter) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(P.counter, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    __syncthreads();
+    if (tile >= P.total_tiles) {
+      done = true;
+      break;
+    }
+    // field of this tile: last f with tile_start[f] <= tile
+    int lo = 0, hi = P.nfields;  // tile_start[lo] <= tile < tile_start[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (P.tile_start[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const FieldDesc fd = P.fields[lo];
+    const int64_t start = (tile - P.tile_start[lo]) * (int64_t)P.tile;
+    const int64_t len = min((int64_t)P.tile, fd.n - start);
+    const uint64_t *a = fd.a + start;
+    const uint64_t *b = (OP == IVC_OP_ADD ? fd.b : fd.c) + start;
+    uint64_t *c = fd.c + start;
+    const bool vec2 = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+                        reinterpret_cast<uintptr_t>(c)) & 15u) == 0;
+    if (OP == IVC_OP_ADD)
+      fused_range<MAP>(a, b, c, len, vec2, threadIdx.x, blockDim.x, OpAdd{}, F, tab_t, tab_p,
+                       flags);
+    else
+      fused_range<MAP>(a, b, c, len, vec2, threadIdx.x, blockDim.x, OpAxpy{fd.alpha}, F, tab_t,
+                       tab_p, flags);
+  }
+  if (!done && threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_TIMEOUT);
+}
+
+// Tiles per field and their prefix sums (one block; nfields is small).
+__global__ void k_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t acc = 0;
+    for (int f = 0; f < nfields; ++f) {
+      tile_start[f] = acc;
+      const int64_t n = fields[f].n > 0 ? fields[f].n : 0;
+      acc += (n + tile - 1) / tile;
+    }
+    tile_start[nfields] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+size_t table_smem_bytes(const DevFormat &F, int map) {
+  return map == MAP_TANH ? 0 : (size_t)(F.nent_t + F.nent_p) * sizeof(TabEntry);
+}
+
+#define IVC_DISPATCH_MAP(map, KERNEL, ...)                                                    \
+  switch (map) {                                                                              \
+    case MAP_UNIFORM: KERNEL<MAP_UNIFORM><<<s.grid, s.block, s.smem, st>>>(__VA_ARGS__); break; \
+    case MAP_TANH: KERNEL<MAP_TANH><<<s.grid, s.block, s.smem, st>>>(__VA_ARGS__); break;       \
+    default: KERNEL<MAP_FRACSPLIT><<<s.grid, s.block, s.smem, st>>>(__VA_ARGS__); break;       \
+  }                                                                                           \
+  return cudaGetLastError()
+
+cudaError_t launch_compress(int map, const DevFormat &F, const float *xyz, int layout, int64_t ld,
+                            int64_t n, uint64_t *w, ivc_counts *counts, const LaunchShape &s,
+                            cudaStream_t st) {
+  IVC_DISPATCH_MAP(map, k_compress, F, xyz, layout, ld, n, w, counts);
+}
+
+cudaError_t launch_decompress(int map, const DevFormat &F, const uint64_t *w, int64_t n,
+                              float *xyz, int layout, int64_t ld, const LaunchShape &s,
+                              cudaStream_t st) {
+  IVC_DISPATCH_MAP(map, k_decompress, F, w, n, xyz, layout, ld);
+}
+
+cudaError_t launch_add(int map, const DevFormat &F, const uint64_t *a, const uint64_t *b,
+                       uint64_t *c, int64_t n, const LaunchShape &s, cudaStream_t st) {
+  IVC_DISPATCH_MAP(map, k_add, F, a, b, c, n, s.vec2);
+}
+
+cudaError_t launch_axpy(int map, const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
+                        int64_t n, const LaunchShape &s, cudaStream_t st) {
+  IVC_DISPATCH_MAP(map, k_axpy, F, alpha, x, y, n, s.vec2);
+}
+
+cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t *v,
+                          const uint64_t *f, const float *rho, uint64_t *v_out, uint64_t *m_out,
+                          int64_t n, const LaunchShape &s, cudaStream_t st) {
+  IVC_DISPATCH_MAP(map, k_update, F, dt, v, f, rho, v_out, m_out, n);
+}
+
+cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P,
+                           const LaunchShape &s, cudaStream_t st) {
+  if (op == IVC_OP_ADD) {
+    switch (map) {
+      case MAP_UNIFORM: k_batched<MAP_UNIFORM, IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, P); break;
+      case MAP_TANH: k_batched<MAP_TANH, IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, P); break;
+      default: k_batched<MAP_FRACSPLIT, IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, P); break;
+    }
+  } else {
+    switch (map) {
+      case MAP_UNIFORM: k_batched<MAP_UNIFORM, IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, P); break;
+      case MAP_TANH: k_batched<MAP_TANH, IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, P); break;
+      default: k_batched<MAP_FRACSPLIT, IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, P); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,
+                             cudaStream_t st) {
+  k_tile_scan<<<1, 32, 0, st>>>(fields, nfields, tile, tile_start);
+  return cudaGetLastError();
+}
+
+template <int MAP>
+static const void *kernel_ptr(int kind) {
+  switch (kind) {
+    case K_COMPRESS: return (const void *)k_compress<MAP>;
+    case K_DECOMPRESS: return (const void *)k_decompress<MAP>;
+    case K_ADD: return (const void *)k_add<MAP>;
+    case K_AXPY: return (const void *)k_axpy<MAP>;
+    case K_UPDATE: return (const void *)k_update<MAP>;
+    case K_BATCH_ADD: return (const void *)k_batched<MAP, IVC_OP_ADD>;
+    default: return (const void *)k_batched<MAP, IVC_OP_AXPY>;
+  }
+}
+
+int occupancy(int map, int kind, int block, size_t smem) {
+  const void *k = map == MAP_UNIFORM ? kernel_ptr<MAP_UNIFORM>(kind)
+                  : map == MAP_TANH  ? kernel_ptr<MAP_TANH>(kind)
+                                     : kernel_ptr<MAP_FRACSPLIT>(kind);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+}  // namespace ivc

@@ -1,0 +1,335 @@
+"""ctypes binding of the C ABI in ``include/ivc.h`` (library ``_build/libivc.so``).
+
+Argument marshalling only: every entry point of the C ABI is exposed under
+its own name with the same arguments (pointers as Python ints, stream as a
+``cudaStream_t`` integer handle).  Small tensor helpers (``compress``,
+``decompress``, ``add`` ...) take torch CUDA tensors, pass their device
+pointers and the current stream, and raise ``IvcError`` on a non-OK status.
+There is no fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+IVC_OK, IVC_ERR_ARG, IVC_ERR_FORMAT, IVC_ERR_ALIGN, IVC_ERR_CUDA = 0, 1, 2, 3, 4
+IVC_ERR_TIMEOUT, IVC_ERR_NOMEM, IVC_ERR_UNSUPPORTED = 5, 6, 7
+IVC_AOS, IVC_SOA = 0, 1
+IVC_MAP_UNIFORM, IVC_MAP_TANH, IVC_MAP_FRACSPLIT = 0, 1, 2
+IVC_F16, IVC_BF16 = 0, 1
+IVC_OP_ADD, IVC_OP_AXPY = 0, 1
+IVC_STATS_LEN = 11
+
+
+class IvcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class ivc_format(ctypes.Structure):
+    _fields_ = [("sign_bits", ctypes.c_int32), ("exp_bits", ctypes.c_int32),
+                ("man_bits", ctypes.c_int32), ("phi_bits", ctypes.c_int32),
+                ("theta_bits", ctypes.c_int32), ("exp_bias", ctypes.c_int32),
+                ("map", ctypes.c_int32), ("underflow_mode", ctypes.c_int32),
+                ("overflow_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("nphi_max_p1", ctypes.c_int64)]
+
+
+class ivc_counts(ctypes.Structure):
+    _fields_ = [("n_overflow", ctypes.c_ulonglong), ("n_underflow", ctypes.c_ulonglong),
+                ("n_nonfinite", ctypes.c_ulonglong)]
+
+
+class ivc_field(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("alpha", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+class ivc_launch_config(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("vec_per_thread", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_F = ctypes.c_float
+_I = ctypes.c_int
+_FMT = ctypes.POINTER(ivc_format)
+_SIGS = {
+    "ivc_format_default": [_FMT],
+    "ivc_format_validate": [_FMT],
+    "ivc_release_tables": [],
+    "ivc_compress": [_FMT, _P, _I, _I64, _I64, _P, _P, _P],
+    "ivc_decompress": [_FMT, _P, _I64, _P, _I, _I64, _P],
+    "ivc_add": [_FMT, _P, _P, _P, _I64, _P],
+    "ivc_add_cfg": [_FMT, _P, _P, _P, _I64, ctypes.POINTER(ivc_launch_config), _P],
+    "ivc_axpy": [_FMT, _F, _P, _P, _I64, _P],
+    "ivc_pointwise_update": [_FMT, _F, _P, _P, _P, _P, _P, _I64, _P],
+    "ivc_f32_add": [_I, _P, _P, _P, _I64, _I64, _P],
+    "ivc_f32_axpy": [_I, _F, _P, _P, _I64, _I64, _P],
+    "ivc_half_add": [_I, _P, _P, _P, _I64, _P],
+    "ivc_half_axpy": [_I, _F, _P, _P, _I64, _P],
+    "ivc_half_from_f32": [_I, _P, _P, _I64, _P],
+    "ivc_half_to_f32": [_I, _P, _P, _I64, _P],
+    "ivc_error_stats": [_P, _P, _I64, _P, _P],
+    "ivc_plan_batched": [_FMT, _I, ctypes.POINTER(ivc_field), _I, _P,
+                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ivc_launch_config), _P,
+                         ctypes.POINTER(ctypes.c_void_p)],
+    "ivc_launch_plan": [_P, _P],
+    "ivc_launch_plan_direct": [_P, _P],
+    "ivc_plan_status": [_P, _P],
+    "ivc_plan_destroy": [_P],
+    "ivc_tune": [_FMT, _I, _P, _P, _P, _I64, _P, ctypes.POINTER(ivc_launch_config)],
+}
+EXPORTS = sorted(list(_SIGS) + ["ivc_status_string", "ivc_version"])
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libivc.so (building it with nvcc when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libivc.so not built ({_build.LIB}); run paper_2003_02633_gb300.build")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.ivc_status_string.argtypes = [ctypes.c_int]
+    lib.ivc_status_string.restype = ctypes.c_char_p
+    lib.ivc_version.argtypes = []
+    lib.ivc_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load().ivc_status_string(int(s)).decode()
+
+
+def _chk(s: int, where: str) -> None:
+    if s != IVC_OK:
+        raise IvcError(s, where)
+
+
+def make_format(sign_bits=0, exp_bits=7, man_bits=22, phi_bits=17, theta_bits=18, exp_bias=80,
+                map=IVC_MAP_UNIFORM, underflow_mode=0, overflow_mode=0, gamma=0.5,
+                nphi_max_p1=0) -> ivc_format:
+    """An ivc_format; the defaults are the primary layout <0,7,22>-17-18."""
+    return ivc_format(sign_bits, exp_bits, man_bits, phi_bits, theta_bits, exp_bias, map,
+                      underflow_mode, overflow_mode, 0, float(gamma), int(nphi_max_p1))
+
+
+def default_format() -> ivc_format:
+    f = ivc_format()
+    _chk(load().ivc_format_default(ctypes.byref(f)), "ivc_format_default")
+    return f
+
+
+# ----------------------------------------------------------- tensor helpers
+
+def _stream(stream=None) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def compress(fmt, xyz, out=None, counts=None, stream=None):
+    """(n,3) float32 CUDA tensor (AoS) -> (n,) int64 tensor of packed words."""
+    import torch
+    n = xyz.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=xyz.device)
+    _chk(load().ivc_compress(ctypes.byref(fmt), _ptr(xyz), IVC_AOS, 0, n, _ptr(out),
+                             _ptr(counts), _stream(stream)), "ivc_compress")
+    return out
+
+
+def compress_soa(fmt, xyz_rows, ld, n, out, stream=None):
+    """SoA input: xyz_rows a float32 CUDA tensor holding rows x, y, z at stride ld."""
+    _chk(load().ivc_compress(ctypes.byref(fmt), _ptr(xyz_rows), IVC_SOA, ld, n, _ptr(out),
+                             None, _stream(stream)), "ivc_compress")
+    return out
+
+
+def decompress(fmt, w, out=None, stream=None):
+    """(n,) int64 word tensor -> (n,3) float32 tensor (AoS)."""
+    import torch
+    n = w.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=w.device)
+    _chk(load().ivc_decompress(ctypes.byref(fmt), _ptr(w), n, _ptr(out), IVC_AOS, 0,
+                               _stream(stream)), "ivc_decompress")
+    return out
+
+
+def add(fmt, a, b, out=None, cfg=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(a)
+    c = ctypes.byref(cfg) if cfg is not None else None
+    _chk(load().ivc_add_cfg(ctypes.byref(fmt), _ptr(a), _ptr(b), _ptr(out), a.shape[0], c,
+                            _stream(stream)), "ivc_add")
+    return out
+
+
+def axpy(fmt, alpha, x, y, stream=None):
+    """In place: y <- compress(alpha * x^ + y^)."""
+    _chk(load().ivc_axpy(ctypes.byref(fmt), float(alpha), _ptr(x), _ptr(y), x.shape[0],
+                         _stream(stream)), "ivc_axpy")
+    return y
+
+
+def pointwise_update(fmt, dt, v, f, rho=None, v_out=None, m_out=None, stream=None):
+    import torch
+    if v_out is None:
+        v_out = torch.empty_like(v)
+    _chk(load().ivc_pointwise_update(ctypes.byref(fmt), float(dt), _ptr(v), _ptr(f), _ptr(rho),
+                                     _ptr(v_out), _ptr(m_out), v.shape[0], _stream(stream)),
+         "ivc_pointwise_update")
+    return v_out, m_out
+
+
+def f32_add(a, b, out=None, layout=IVC_AOS, ld=0, n=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(a)
+    n = a.shape[0] if n is None else n
+    _chk(load().ivc_f32_add(layout, _ptr(a), _ptr(b), _ptr(out), ld, n, _stream(stream)),
+         "ivc_f32_add")
+    return out
+
+
+def f32_axpy(alpha, x, y, layout=IVC_AOS, ld=0, n=None, stream=None):
+    n = x.shape[0] if n is None else n
+    _chk(load().ivc_f32_axpy(layout, float(alpha), _ptr(x), _ptr(y), ld, n, _stream(stream)),
+         "ivc_f32_axpy")
+    return y
+
+
+def half_from_f32(kind, xyz, out=None, stream=None):
+    import torch
+    n = xyz.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.int16, device=xyz.device)
+    _chk(load().ivc_half_from_f32(kind, _ptr(xyz), _ptr(out), n, _stream(stream)),
+         "ivc_half_from_f32")
+    return out
+
+
+def half_to_f32(kind, h, out=None, stream=None):
+    import torch
+    n = h.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=h.device)
+    _chk(load().ivc_half_to_f32(kind, _ptr(h), _ptr(out), n, _stream(stream)), "ivc_half_to_f32")
+    return out
+
+
+def half_add(kind, a, b, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(a)
+    _chk(load().ivc_half_add(kind, _ptr(a), _ptr(b), _ptr(out), a.shape[0], _stream(stream)),
+         "ivc_half_add")
+    return out
+
+
+def half_axpy(kind, alpha, x, y, stream=None):
+    _chk(load().ivc_half_axpy(kind, float(alpha), _ptr(x), _ptr(y), x.shape[0], _stream(stream)),
+         "ivc_half_axpy")
+    return y
+
+
+def error_stats(x, xh, out=None, stream=None):
+    """FP64 error statistics of xh against x; returns the accumulated 11 doubles."""
+    import torch
+    if out is None:
+        out = torch.zeros(IVC_STATS_LEN, dtype=torch.float64, device=x.device)
+    _chk(load().ivc_error_stats(_ptr(x), _ptr(xh), x.shape[0], _ptr(out), _stream(stream)),
+         "ivc_error_stats")
+    return out
+
+
+def stats_dict(acc) -> dict:
+    """Named statistics from the accumulated ivc_error_stats output."""
+    v = [float(x) for x in acc.tolist()]
+    n = max(v[0], 1.0)
+    mean = v[1] / n
+    var = max(0.0, (v[2] - v[1] * v[1] / n) / max(n - 1, 1.0))
+    return {"n": int(v[0]), "mean": mean, "sd": var ** 0.5, "max": v[3], "mean_rel": v[4] / n,
+            "max_rel": v[5], "rms_ang": (v[6] / n) ** 0.5, "max_ang": v[7],
+            "rms_mag_rel": (v[8] / n) ** 0.5, "max_mag_rel": v[9], "n_nonfinite_out": int(v[10])}
+
+
+class BatchedPlan:
+    """ivc_plan_batched over a list of (a, b, c, alpha) tensor fields."""
+
+    def __init__(self, fmt, op, fields, cfg=None, stream=None):
+        import torch
+        L = load()
+        arr = (ivc_field * len(fields))()
+        for i, (a, b, c, alpha) in enumerate(fields):
+            arr[i] = ivc_field(_ptr(a), _ptr(b) if b is not None else None, _ptr(c), a.shape[0],
+                               float(alpha), 0.0)
+        self._keep = (fields, arr)
+        ws = ctypes.c_size_t(0)
+        c = ctypes.byref(cfg) if cfg is not None else None
+        _chk(L.ivc_plan_batched(ctypes.byref(fmt), op, arr, len(fields), None, ctypes.byref(ws),
+                                c, _stream(stream), None), "ivc_plan_batched(size)")
+        dev = fields[0][0].device
+        self.workspace = torch.empty(ws.value + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.plan = ctypes.c_void_p()
+        _chk(L.ivc_plan_batched(ctypes.byref(fmt), op, arr, len(fields), aligned,
+                                ctypes.byref(ws), c, _stream(stream), ctypes.byref(self.plan)),
+             "ivc_plan_batched")
+
+    def launch(self, stream=None, graph=True):
+        fn = load().ivc_launch_plan if graph else load().ivc_launch_plan_direct
+        _chk(fn(self.plan, _stream(stream)), "ivc_launch_plan")
+
+    def status(self, stream=None) -> int:
+        return load().ivc_plan_status(self.plan, _stream(stream))
+
+    def close(self):
+        if self.plan:
+            load().ivc_plan_destroy(self.plan)
+            self.plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tune(fmt, op, a, b, c, stream=None) -> ivc_launch_config:
+    best = ivc_launch_config()
+    _chk(load().ivc_tune(ctypes.byref(fmt), op, _ptr(a), _ptr(b), _ptr(c), a.shape[0],
+                         _stream(stream), ctypes.byref(best)), "ivc_tune")
+    return best

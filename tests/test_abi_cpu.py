@@ -1,0 +1,89 @@
+"""C-ABI library: it builds, loads and exports every symbol include/ivc.h
+declares; host-only entry points (format set-up, validation, status text) and
+argument checks that return before any device work run here without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2003_02633_gb300 import ivc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ivc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ivc_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ivc.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(ivc.EXPORTS) == names
+
+
+def test_version_and_status_strings(lib):
+    assert b"sm_103a" in lib.ivc_version()
+    assert ivc.status_string(ivc.IVC_OK) == "ok"
+    assert "format" in ivc.status_string(ivc.IVC_ERR_FORMAT)
+    assert ivc.status_string(99) == "unknown status"
+
+
+def test_default_format_is_primary_layout(lib):
+    f = ivc.default_format()
+    assert (f.sign_bits, f.exp_bits, f.man_bits, f.phi_bits, f.theta_bits, f.exp_bias) == \
+        (0, 7, 22, 17, 18, 80)
+    assert lib.ivc_format_validate(ctypes.byref(f)) == ivc.IVC_OK
+
+
+@pytest.mark.parametrize("kw", [
+    dict(exp_bits=9), dict(man_bits=24), dict(theta_bits=20), dict(phi_bits=40),
+    dict(sign_bits=2), dict(exp_bias=300), dict(map=7), dict(map=1, gamma=0.0),
+    dict(map=2, nphi_max_p1=1), dict(underflow_mode=2),
+])
+def test_invalid_formats_rejected(lib, kw):
+    f = ivc.make_format(**kw)
+    assert lib.ivc_format_validate(ctypes.byref(f)) == ivc.IVC_ERR_FORMAT
+
+
+@pytest.mark.parametrize("kw", [
+    dict(), dict(exp_bits=8, man_bits=23, phi_bits=16, theta_bits=17, exp_bias=127),
+    dict(exp_bits=7, man_bits=23, phi_bits=17, theta_bits=17, exp_bias=80),
+    dict(sign_bits=1, exp_bits=8, man_bits=23, phi_bits=16, theta_bits=16, exp_bias=127),
+    dict(map=2, nphi_max_p1=185363), dict(map=1, gamma=0.5),
+    dict(exp_bits=3, man_bits=4, phi_bits=4, theta_bits=5, exp_bias=3),
+])
+def test_paper_formats_accepted(lib, kw):
+    f = ivc.make_format(**kw)
+    assert lib.ivc_format_validate(ctypes.byref(f)) == ivc.IVC_OK
+
+
+def test_argument_errors_before_device_work(lib):
+    f = ivc.default_format()
+    bad = ivc.make_format(exp_bits=9)
+    assert lib.ivc_compress(ctypes.byref(f), None, 0, 0, -1, None, None, None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_compress(ctypes.byref(f), None, 5, 0, 1, None, None, None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_compress(ctypes.byref(bad), None, 0, 0, 1, None, None, None) == \
+        ivc.IVC_ERR_FORMAT
+    assert lib.ivc_add(ctypes.byref(f), None, None, None, -3, None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_f32_add(0, None, None, None, 0, -1, None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_f32_add(1, None, None, None, 2, 5, None) == ivc.IVC_ERR_ARG  # ld < n
+    assert lib.ivc_half_add(9, None, None, None, 1, None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_error_stats(None, None, -1, None, None) == ivc.IVC_ERR_ARG
+    ws = ctypes.c_size_t(0)
+    assert lib.ivc_plan_batched(ctypes.byref(f), 0, None, 0, None, ctypes.byref(ws), None, None,
+                                None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_plan_batched(ctypes.byref(f), 0, None, 4, None, ctypes.byref(ws), None, None,
+                                None) == ivc.IVC_OK
+    assert ws.value >= 4 * 48
+    assert lib.ivc_launch_plan(None, None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_plan_destroy(None) == ivc.IVC_ERR_ARG
