@@ -68,15 +68,28 @@ TabEntry entry_of(long double c, long double s) {
   return e;
 }
 
-// Head table of the folded grid pi b / (2D): entries at b = 256 i.
+// Head-table geometry of the folded grid pi b / (2D), b in [0, D/2]: entries at
+// b = i 2^s, the remainder rounded to the nearest entry; s is the smallest step
+// with at most 1024 entries.
+int table_entries(int D, int s) {
+  return s == 0 ? D / 2 + 1 : ((D / 2 + (1 << (s - 1))) >> s) + 1;
+}
+
+int table_shift(int D) {
+  int s = 0;
+  while (table_entries(D, s) > 1024) ++s;
+  return s;
+}
+
 void uniform_table(int D, std::vector<TabEntry> &out) {
-  const int nent = ((D / 2) >> 8) + 1;
+  const int s = table_shift(D);
+  const int nent = table_entries(D, s);
   for (int i = 0; i < nent; ++i) {
     if (i == 0) {
       out.push_back(TabEntry{1.0f, 0.0f, 0.0f, 0.0f});
       continue;
     }
-    const long double a = kPiL * (256.0L * i) / (2.0L * D);
+    const long double a = kPiL * (long double)((long long)i << s) / (2.0L * D);
     out.push_back(entry_of(cosl(a), sinl(a)));
   }
 }
@@ -215,8 +228,10 @@ ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
   F->tmax_p = (float)g.M - 0.25f;
   F->Dt = g.N;
   F->Dp = 2 * g.M;
-  F->nent_t = ((F->Dt / 2) >> 8) + 1;
-  F->nent_p = ((F->Dp / 2) >> 8) + 1;
+  F->st = table_shift(F->Dt);
+  F->sp = table_shift(F->Dp);
+  F->nent_t = table_entries(F->Dt, F->st);
+  F->nent_p = table_entries(F->Dp, F->sp);
   ff_split(kPiL / (2.0L * F->Dt), F->Kt_h, F->Kt_l);
   ff_split(kPiL / (2.0L * F->Dp), F->Kp_h, F->Kp_l);
   F->tab = ts.dev;
@@ -376,6 +391,10 @@ ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t 
   if (!aligned(a, 8) || !aligned(b, 8) || !aligned(c, 8)) return IVC_ERR_ALIGN;
   const int vec2 = (aligned(a, 16) && aligned(b, 16) && aligned(c, 16) &&
                     !(cfg && cfg->vec_per_thread == 1)) ? 1 : 0;
+  if (vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F)) {
+    const LaunchShape s = default_shape(map, K_ADD_FAST, F, n, 1, cfg);
+    return cuda_status(launch_add_fast(F, a, b, c, n, s, stream));
+  }
   const LaunchShape s = default_shape(map, K_ADD, F, n, vec2, cfg);
   return cuda_status(launch_add(map, F, a, b, c, n, s, stream));
 }
@@ -396,6 +415,10 @@ ivc_status ivc_axpy(const ivc_format *fmt, float alpha, const uint64_t *x, uint6
   if (!x || !y) return IVC_ERR_ARG;
   if (!aligned(x, 8) || !aligned(y, 8)) return IVC_ERR_ALIGN;
   const int vec2 = (aligned(x, 16) && aligned(y, 16)) ? 1 : 0;
+  if (vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F)) {
+    const LaunchShape s = default_shape(map, K_AXPY_FAST, F, n, 1, nullptr);
+    return cuda_status(launch_axpy_fast(F, alpha, x, y, n, s, stream));
+  }
   const LaunchShape s = default_shape(map, K_AXPY, F, n, vec2, nullptr);
   return cuda_status(launch_axpy(map, F, alpha, x, y, n, s, stream));
 }
@@ -413,6 +436,12 @@ ivc_status ivc_pointwise_update(const ivc_format *fmt, float dt, const uint64_t 
   if (!aligned(v, 8) || !aligned(f, 8) || !aligned(v_out, 8) || (m_out && !aligned(m_out, 8)) ||
       (rho && !aligned(rho, 4)))
     return IVC_ERR_ALIGN;
+  const bool al = aligned(v, 16) && aligned(f, 16) && aligned(v_out, 16) &&
+                  (!m_out || aligned(m_out, 16)) && (!rho || aligned(rho, 8));
+  if (al && map == IVC_MAP_UNIFORM && fast::is_primary(F)) {
+    const LaunchShape s = default_shape(map, K_UPDATE_FAST, F, n, 1, nullptr);
+    return cuda_status(launch_update_fast(F, dt, v, f, rho, v_out, m_out, n, s, stream));
+  }
   const LaunchShape s = default_shape(map, K_UPDATE, F, n, 0, nullptr);
   return cuda_status(launch_update(map, F, dt, v, f, rho, v_out, m_out, n, s, stream));
 }
@@ -467,7 +496,8 @@ ivc_status ivc_plan_batched(const ivc_format *fmt, ivc_op op, const ivc_field *f
   }
   p->op = op;
   cudaGetDevice(&p->device);
-  const int tile = (cfg && cfg->tile > 0) ? cfg->tile : 8192;
+  int tile = (cfg && cfg->tile > 0) ? cfg->tile : 8192;
+  tile = (tile + 1) & ~1;  // even tiles keep 16-byte alignment inside a field
   char *ws = static_cast<char *>(workspace);
   FieldDesc *d_fields = reinterpret_cast<FieldDesc *>(ws);
   ws += round_up(sizeof(FieldDesc) * (size_t)nfields, 256);
@@ -494,7 +524,9 @@ ivc_status ivc_plan_batched(const ivc_format *fmt, ivc_op op, const ivc_field *f
     return IVC_ERR_CUDA;
   }
   p->P = PlanDev{d_fields, d_tiles, d_counter, d_status, total_tiles, nfields, tile};
-  const int kind = op == IVC_OP_ADD ? K_BATCH_ADD : K_BATCH_AXPY;
+  const bool fastp = p->map == IVC_MAP_UNIFORM && fast::is_primary(p->F);
+  const int kind = op == IVC_OP_ADD ? (fastp ? K_BATCH_ADD_FAST : K_BATCH_ADD)
+                                    : (fastp ? K_BATCH_AXPY_FAST : K_BATCH_AXPY);
   LaunchShape s;
   s.block = (cfg && cfg->block > 0 && cfg->block <= 256) ? cfg->block : 256;
   s.vec2 = 1;
@@ -580,18 +612,30 @@ ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const u
   }
   float best_ms = 1e30f;
   ivc_launch_config bc{256, vec2 ? 2 : 1, 8192, 0};
+  const bool fast_kind = vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F);
   for (int blk : blocks) {
     const size_t smem = table_smem_bytes(F, map);
-    const int occ = occupancy(map, kind, blk, smem);
+    const int occ = occupancy(map, fast_kind ? (op == IVC_OP_ADD ? K_ADD_FAST : K_AXPY_FAST) : kind,
+                              blk, smem);
     for (int bps = 1; bps <= occ; bps *= 2) {
       ivc_launch_config cfg{blk, vec2 ? 2 : 1, 8192, bps};
       LaunchShape s = default_shape(map, kind, F, n, vec2, &cfg);
       float ms_min = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, stream);
-        cudaError_t e = op == IVC_OP_ADD ? launch_add(map, F, a, b, c, n, s, stream)
-                                         : launch_axpy(map, F, 0.7f, a, const_cast<uint64_t *>(b),
-                                                       n, s, stream);
+        const bool fastp = vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F);
+        cudaError_t e;
+        if (fastp) {
+          const LaunchShape sf =
+              default_shape(map, op == IVC_OP_ADD ? K_ADD_FAST : K_AXPY_FAST, F, n, 1, &cfg);
+          e = op == IVC_OP_ADD
+                  ? launch_add_fast(F, a, b, c, n, sf, stream)
+                  : launch_axpy_fast(F, 0.7f, a, const_cast<uint64_t *>(b), n, sf, stream);
+        } else {
+          e = op == IVC_OP_ADD ? launch_add(map, F, a, b, c, n, s, stream)
+                               : launch_axpy(map, F, 0.7f, a, const_cast<uint64_t *>(b), n, s,
+                                             stream);
+        }
         cudaEventRecord(e1, stream);
         if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
           cudaGetLastError();

@@ -1,25 +1,36 @@
 // Device arithmetic of inline 3-vector compression (Trojak & Witherden,
 // arXiv:2003.02633) for sm_103a.
 //
-// Encoding (Sec. 2.1, 2.3, 3).  The magnitude is RN32(|x|) from a
-// double-float sum of squares and a double-float square root; its exponent
-// is rebiased and its mantissa truncated (Sec. 2.3).  Each angle index is
-// nint(t) (Eq. a_disc): an FP32 estimate of t, good to a few hundredths of a
-// bin, names the one rounding boundary k + 1/2 that can matter, and an
-// error-free sign test of the input against that boundary's direction
-// decides k or k + 1:
-//   theta: sign(y cos(theta_h) - x sin(theta_h)),
-//   phi:   sign(rho cos(phi_h) - z sin(phi_h)),  rho = sqrt(x^2 + y^2),
-// with cos/sin of the boundary angle in double-float (about 2^-44 relative).
-// Exact ties (theta = 0, phi = pi/2) give a zero test value and round up.
+// Every rounding decision the method makes is taken in FP32 arithmetic with a
+// stated error bound; the rare inputs whose decision the bound does not
+// settle are re-evaluated in FP64 (noinline helpers, off the common path).
+//
+// Encoding (Sec. 2.1, 2.3, 3).
+//   magnitude: RN32(|x|) from a double-float sum of squares and a
+//     double-float square root (error < 2^-44); within 2^-42 of an FP32
+//     rounding midpoint the norm is recomputed in FP64.  Exponent rebiased,
+//     mantissa truncated (Sec. 2.3).
+//   angles: n = nint(t) (Eq. a_disc).  An FP32 estimate of t, good to a few
+//     hundredths of a bin, names the one rounding boundary k + 1/2 that can
+//     matter; a side-of-boundary test of the input against that boundary's
+//     direction decides k or k + 1:
+//       theta: sign(y cos(theta_h) - x sin(theta_h)),
+//       phi:   sign(rho cos(phi_h) - z sin(phi_h)),  rho = sqrt(x^2 + y^2),
+//     with cos/sin of the boundary in double-float (about 2^-42 relative) and
+//     error-free products; |test| below 2^-40 of its terms -> FP64 test.
+//     Exact ties (theta = 0, phi = pi/2) give a test value of exactly zero and
+//     round up.
 //
 // Decoding (Eq. a_inv, Eq. cart2sphere).  theta^ = pi (2 n_theta - N) / N and
-// phi^ = pi (2 n_phi) / (2 M) are rational multiples of pi.  Every such angle
-// pi m / D is folded exactly, in integers, onto [0, pi/4]; cos and sin there
-// come from a small table of double-float values at multiples of 256 units
-// plus a Taylor step for the remaining < 256 units (pi / (2D) each).  The
-// products r cos(theta) sin(phi) etc. are formed in double-float and rounded
-// away from zero to FP32 with one directed-rounding FMA.
+// phi^ = pi (2 n_phi) / (2M) are rational multiples of pi.  Each angle pi m / D
+// is folded exactly, in integers, onto [0, pi/4]; cos and sin there come from
+// a shared-memory table of double-float values at multiples of 2^s units
+// (pi / (2D) each; at most 1024 entries) plus a Taylor step for the signed
+// remainder.
+// The products r cos(theta) sin(phi) etc. are formed in double-float and
+// rounded away from zero with a directed-rounding FMA; when the value lies
+// within 2^-40 (relative) of an FP32 grid point the vector is decoded again
+// in FP64.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -27,6 +38,12 @@
 namespace ivc {
 
 enum : int { MAP_UNIFORM = 0, MAP_TANH = 1, MAP_FRACSPLIT = 2 };
+
+// Relative error bounds of the FP32 paths (see the design notes for the
+// derivation); the ambiguity thresholds include a safety factor.
+constexpr float kDecodeAmbig = 9.094947e-13f;   // 2^-40
+constexpr float kSideAmbig = 9.094947e-13f;     // 2^-40
+constexpr float kNormAmbig = 2.2737368e-13f;    // 2^-42
 
 // cos/sin of one table angle, each as head + tail.
 struct __align__(16) TabEntry {
@@ -54,6 +71,7 @@ struct DevFormat {
   // uniform / fractional split: folded sin/cos tables (theta then phi)
   int32_t Dt, Dp;                   // theta grid pi m / N, phi grid pi m / (2M)
   int32_t nent_t, nent_p;           // table entries
+  int32_t st, sp;                   // table step 2^s units
   float Kt_h, Kt_l, Kp_h, Kp_l;     // pi / (2 D) in double-float
   const TabEntry *tab;              // global, nent_t + nent_p entries
   uint64_t div_magic;               // ceil(2^64 / (N + 1)) for the split
@@ -64,14 +82,35 @@ struct DevFormat {
 };
 
 // --------------------------------------------------------------------------
-// Double-float helpers.
+// Exact integer folding of pi m / D onto [0, pi/4].
 
-// cos and sin of pi * b / (2D), b in [0, D/2], from the head table and a
-// Taylor step.  Returns magnitudes (both >= 0).
-__device__ __forceinline__ void sincos_folded(int b, const TabEntry *__restrict__ tab,
-                                              float Kh, float Kl, FF &c, FF &s) {
-  const int h = b >> 8;
-  const float lf = (float)(b & 255);
+struct Fold {
+  int b;       // folded angle pi b / (2D), b in [0, D/2]
+  bool swap;   // cos and sin exchange
+  bool cneg;   // cos negative
+  bool sneg;   // sin negative
+};
+
+__device__ __forceinline__ Fold fold_grid(int m, int D) {
+  Fold f;
+  f.sneg = m < 0;
+  const int a = abs(m);
+  f.cneg = 2 * a > D;
+  const int a1 = f.cneg ? D - a : a;   // pi a1 / D in [0, pi/2]
+  f.swap = 4 * a1 > D;
+  f.b = f.swap ? D - 2 * a1 : 2 * a1;  // pi b / (2D) in [0, pi/4]
+  return f;
+}
+
+// cos and sin (both >= 0) of pi b / (2D) from the head table (entries at
+// b = h 2^s) and a Taylor step over the signed remainder l = b - h 2^s,
+// |l| <= 2^(s-1) (h = b / 2^s rounded to nearest): relative error below 2^-42.
+// Fast2Sum preconditions: |cA| >= |sA beta| always; |sA| >= |cA beta| when
+// h >= 1 (tan A >= A >= |beta|), and sA = 0 when h = 0 (then l >= 0).
+__device__ __forceinline__ void sincos_folded(int b, const TabEntry *__restrict__ tab, int s,
+                                              float Kh, float Kl, FF &c, FF &sn) {
+  const int h = (s > 0) ? ((b + (1 << (s - 1))) >> s) : b;
+  const float lf = (float)(b - (h << s));
   const TabEntry e = tab[h];
   // beta = l pi / (2D) in double-float
   const float bh = lf * Kh;
@@ -100,32 +139,41 @@ __device__ __forceinline__ void sincos_folded(int b, const TabEntry *__restrict_
   Sl = fmaf(e.ch, stail, Sl);
   Sl = fmaf(e.cl, bh, Sl);
   c.h = Ch; c.l = Cl;
-  s.h = Sh; s.l = Sl;
+  sn.h = Sh; sn.l = Sl;
 }
 
-// cos and sin of pi m / D for integer m in [-D, D] (D <= 2^20): magnitudes in
-// c, s and their signs.
+// cos and sin of pi m / D (m in [-D, D]): magnitudes and signs.
 __device__ __forceinline__ void sincospi_grid(int m, int D, const TabEntry *__restrict__ tab,
-                                              float Kh, float Kl, FF &c, FF &s, bool &cneg,
-                                              bool &sneg) {
-  sneg = m < 0;
-  const int a = abs(m);
-  cneg = 2 * a > D;
-  const int a1 = cneg ? D - a : a;          // pi a1 / D in [0, pi/2]
-  const bool swap = 4 * a1 > D;
-  const int b = swap ? D - 2 * a1 : 2 * a1;  // pi b / (2D) in [0, pi/4]
+                                              int s, float Kh, float Kl, FF &c, FF &sn,
+                                              bool &cneg, bool &sneg) {
+  const Fold f = fold_grid(m, D);
+  cneg = f.cneg;
+  sneg = f.sneg;
   FF cc, ss;
-  sincos_folded(b, tab, Kh, Kl, cc, ss);
-  c = swap ? ss : cc;
-  s = swap ? cc : ss;
+  sincos_folded(f.b, tab, s, Kh, Kl, cc, ss);
+  c = f.swap ? ss : cc;
+  sn = f.swap ? cc : ss;
+}
+
+// FP64 cos and sin of pi m / D (signed), from the exact fold.
+static __device__ __noinline__ void sincospi_grid_f64(int m, int D, double &c, double &s) {
+  const Fold f = fold_grid(m, D);
+  double sb, cb;
+  sincospi((double)f.b / (2.0 * (double)D), &sb, &cb);
+  const double cc = f.swap ? sb : cb;
+  const double ss = f.swap ? cb : sb;
+  c = f.cneg ? -cc : cc;
+  s = f.sneg ? -ss : ss;
 }
 
 __device__ __forceinline__ FF neg_if(FF v, bool n) {
   return n ? FF{-v.h, -v.l} : v;
 }
 
-// a * c - b * s >= 0 for exact FP32 a, b and double-float c, s.
-__device__ __forceinline__ bool side_ge(float a, float a_l, FF c, float b, FF s) {
+// Side test a c - b s for exact FP32 a (+ tail a_l), b and double-float c, s.
+// Returns +1 / 0 (for "< 0") when settled, -1 when |value| is within the
+// error bound.
+__device__ __forceinline__ int side_ge(float a, float a_l, FF c, float b, FF s) {
   const float p1 = a * c.h;
   const float e1 = fmaf(a, c.h, -p1);
   const float p2 = b * s.h;
@@ -135,23 +183,43 @@ __device__ __forceinline__ bool side_ge(float a, float a_l, FF c, float b, FF s)
   lo = fmaf(-b, s.l, lo);
   lo = fmaf(a_l, c.h, lo);
   const float d = (p1 - p2) + lo;
-  return d >= 0.0f;
+  const float bound = kSideAmbig * (fabsf(p1) + fabsf(p2));
+  if (fabsf(d) <= bound && d != 0.0f) return -1;
+  if (d == 0.0f && bound != 0.0f && (p1 != p2 || lo != 0.0f)) return -1;
+  return d >= 0.0f ? 1 : 0;
 }
 
-// Round-up of r * (a * b) for non-negative double-floats a, b and FP32 r >= 0.
-__device__ __forceinline__ float ru_prod3(float r, FF a, FF b) {
+// Round-up of r * (a * b) for non-negative double-floats a, b; sets amb when
+// the value lies within the decode error bound of an FP32 grid point.
+__device__ __forceinline__ float ru_prod3(float r, FF a, FF b, bool &amb) {
   const float P = a.h * b.h;
   const float Pe = fmaf(a.h, b.h, -P);
   const float Pl = fmaf(a.h, b.l, fmaf(a.l, b.h, Pe));
-  return __fmaf_ru(r, P, r * Pl);
+  const float t = r * Pl;
+  const float d = kDecodeAmbig * (r * P);
+  const float x0 = __fmaf_ru(r, P, t - d);
+  const float x1 = __fmaf_ru(r, P, t + d);
+  amb |= (x0 != x1);
+  return x1;
 }
 
-__device__ __forceinline__ float ru_prod2(float r, FF a) {
-  return __fmaf_ru(r, a.h, r * a.l);
+__device__ __forceinline__ float ru_prod2(float r, FF a, bool &amb) {
+  const float t = r * a.l;
+  const float d = kDecodeAmbig * (r * a.h);
+  const float x0 = __fmaf_ru(r, a.h, t - d);
+  const float x1 = __fmaf_ru(r, a.h, t + d);
+  amb |= (x0 != x1);
+  return x1;
 }
 
 __device__ __forceinline__ float apply_sign(float mag, bool neg) {
   return (neg && mag != 0.0f) ? -mag : mag;
+}
+
+// Round a real value (FP64) away from zero to FP32; exact zero -> +0.
+__device__ __forceinline__ float ra32_f64(double v) {
+  if (v == 0.0) return 0.0f;
+  return v > 0.0 ? __double2float_ru(v) : __double2float_rd(v);
 }
 
 // --------------------------------------------------------------------------
@@ -178,9 +246,36 @@ __device__ __forceinline__ uint64_t pack_angles(int nt, int np, const DevFormat 
   return ((uint64_t)np << F.sh_phi) | (uint64_t)nt;
 }
 
+__device__ __forceinline__ float magnitude_of(uint32_t E, uint32_t mant, const DevFormat &F) {
+  const uint32_t rbits = ((uint32_t)((int)E - F.e_off) << 23) | (mant << F.m_shift);
+  return (E == 0u) ? 0.0f : __uint_as_float(rbits);
+}
+
 // --------------------------------------------------------------------------
-// Decode one word (Eq. a_inv, Eq. cart2sphere).  tab_t / tab_p: theta and phi
-// tables (shared memory for the uniform grids).
+// Decode one word (Eq. a_inv, Eq. cart2sphere).
+
+// FP64 decode of a finite word (the fallback of decode_word).
+template <int MAP>
+static __device__ __noinline__ float3 decode_word_f64(uint64_t w, const DevFormat &F) {
+  const uint32_t E = (uint32_t)(w >> F.sh_e) & F.mask_e;
+  const uint32_t mant = (uint32_t)(w >> F.sh_m) & F.mask_m;
+  int nt, np;
+  unpack_angles<MAP>(w, F, nt, np);
+  double ct, st, cp, sp;
+  if (MAP == MAP_TANH) {
+    const TabEntry et = F.dec_t[nt];
+    const TabEntry ep = F.dec_p[np];
+    ct = (double)et.ch + (double)et.cl;
+    st = (double)et.sh + (double)et.sl;
+    cp = (double)ep.ch + (double)ep.cl;
+    sp = (double)ep.sh + (double)ep.sl;
+  } else {
+    sincospi_grid_f64(2 * nt - F.N, F.Dt, ct, st);
+    sincospi_grid_f64(2 * np, F.Dp, cp, sp);
+  }
+  const double r = (double)magnitude_of(E, mant, F);
+  return make_float3(ra32_f64(r * ct * sp), ra32_f64(r * st * sp), ra32_f64(r * cp));
+}
 
 template <int MAP>
 __device__ __forceinline__ float3 decode_word(uint64_t w, const DevFormat &F,
@@ -201,24 +296,24 @@ __device__ __forceinline__ float3 decode_word(uint64_t w, const DevFormat &F,
     cp = neg_if(FF{ep.ch, ep.cl}, cpn);
     sp = FF{ep.sh, ep.sl};
   } else {
-    sincospi_grid(2 * nt - F.N, F.Dt, tab_t, F.Kt_h, F.Kt_l, ct, st, ctn, stn);
-    sincospi_grid(2 * np, F.Dp, tab_p, F.Kp_h, F.Kp_l, cp, sp, cpn, spn);
+    sincospi_grid(2 * nt - F.N, F.Dt, tab_t, F.st, F.Kt_h, F.Kt_l, ct, st, ctn, stn);
+    sincospi_grid(2 * np, F.Dp, tab_p, F.sp, F.Kp_h, F.Kp_l, cp, sp, cpn, spn);
   }
-  float r;
   if (E == (uint32_t)F.e_all) {
-    if (mant != 0u) return make_float3(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
-                                       __int_as_float(0x7fc00000));
-    r = __int_as_float(0x7f800000);  // infinite magnitude: nonzero directions -> inf
-    const float x = (ct.h != 0.0f && sp.h != 0.0f) ? r : 0.0f;
-    const float y = (st.h != 0.0f && sp.h != 0.0f) ? r : 0.0f;
-    const float z = (cp.h != 0.0f) ? r : 0.0f;
+    const float nan = __int_as_float(0x7fc00000);
+    if (mant != 0u) return make_float3(nan, nan, nan);
+    const float inf = __int_as_float(0x7f800000);  // infinite magnitude
+    const float x = (ct.h != 0.0f && sp.h != 0.0f) ? inf : 0.0f;
+    const float y = (st.h != 0.0f && sp.h != 0.0f) ? inf : 0.0f;
+    const float z = (cp.h != 0.0f) ? inf : 0.0f;
     return make_float3(apply_sign(x, ctn), apply_sign(y, stn), apply_sign(z, cpn));
   }
-  const uint32_t rbits = ((uint32_t)((int)E - F.e_off) << 23) | (mant << F.m_shift);
-  r = (E == 0u) ? 0.0f : __uint_as_float(rbits);
-  const float x = ru_prod3(r, ct, sp);
-  const float y = ru_prod3(r, st, sp);
-  const float z = ru_prod2(r, cp);
+  const float r = magnitude_of(E, mant, F);
+  bool amb = false;
+  const float x = ru_prod3(r, ct, sp, amb);
+  const float y = ru_prod3(r, st, sp, amb);
+  const float z = ru_prod2(r, cp, amb);
+  if (amb) return decode_word_f64<MAP>(w, F);
   return make_float3(apply_sign(x, ctn), apply_sign(y, stn), apply_sign(z, cpn));
 }
 
@@ -228,6 +323,39 @@ __device__ __forceinline__ float3 decode_word(uint64_t w, const DevFormat &F,
 
 __device__ __forceinline__ float pow2f(int e) {  // 2^e for e in [-126, 127]
   return __uint_as_float((uint32_t)(e + 127) << 23);
+}
+
+static __device__ __noinline__ float norm_rn_f64(float xs, float ys, float zs) {
+  const double s = (double)xs * xs + (double)ys * ys + (double)zs * zs;
+  return __double2float_rn(sqrt(s));
+}
+
+template <int MAP>
+static __device__ __noinline__ int side_theta_f64(float xs, float ys, int k, const DevFormat &F) {
+  double c, s;
+  if (MAP == MAP_TANH) {
+    const TabEntry e = F.bnd_t[k];
+    c = (double)e.ch + (double)e.cl;
+    s = (double)e.sh + (double)e.sl;
+  } else {
+    sincospi_grid_f64(2 * k + 1 - F.N, F.Dt, c, s);
+  }
+  return ((double)ys * c - (double)xs * s) >= 0.0 ? 1 : 0;
+}
+
+template <int MAP>
+static __device__ __noinline__ int side_phi_f64(float xs, float ys, float zs, int k,
+                                         const DevFormat &F) {
+  double c, s;
+  if (MAP == MAP_TANH) {
+    const TabEntry e = F.bnd_p[k];
+    c = (double)e.ch + (double)e.cl;
+    s = (double)e.sh + (double)e.sl;
+  } else {
+    sincospi_grid_f64(2 * k + 1, F.Dp, c, s);
+  }
+  const double rho = sqrt((double)xs * xs + (double)ys * ys);
+  return (rho * c - (double)zs * s) >= 0.0 ? 1 : 0;
 }
 
 template <int MAP>
@@ -253,11 +381,7 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
   {
     const uint32_t ub = __float_as_uint(amax);
     const int ex = (int)(ub >> 23);
-    if (ex != 0) {
-      S = 127 - ex;
-    } else {  // subnormal
-      S = 127 - 1 + (__clz((int)(ub & 0x7fffffu)) - 8);
-    }
+    S = (ex != 0) ? 127 - ex : 118 + __clz((int)(ub & 0x7fffffu));
   }
   float xs, ys, zs;
   if (S >= -126 && S <= 127) {
@@ -284,15 +408,23 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
   const float r0 = sh * y0;
   const float rh = fmaf(fmaf(-r0, r0, sh) + sl, hy0, r0);
   const float rl = (fmaf(-rh, rh, sh) + sl) * hy0;
-  const float r32 = rh + rl;
+  float r32 = rh + rl;
+  {
+    // distance of rh + rl from the FP32 rounding midpoints around r32
+    const float half_ulp = __uint_as_float((__float_as_uint(r32) & 0x7f800000u) - (24u << 23));
+    const float dev = fabsf((rh - r32) + rl);
+    // a power of two has its lower midpoint a quarter ulp away: re-check those too
+    if (half_ulp - dev <= kNormAmbig * r32 || (__float_as_uint(r32) & 0x7fffffu) == 0u)
+      r32 = norm_rn_f64(xs, ys, zs);
+  }
   const uint32_t rb = __float_as_uint(r32);
   const int E8 = (int)(rb >> 23) - S;
   int Ef = E8 + F.e_off;
   uint32_t mant = (rb & 0x7fffffu) >> F.m_shift;
-  bool over = inf_in || E8 > 254 || Ef > F.e_maxn;
-  bool under = !over && (E8 < 1 || Ef < 1);
+  const bool over = inf_in || E8 > 254 || Ef > F.e_maxn;
+  const bool under = !over && (E8 < 1 || Ef < 1);
 
-  // theta: estimate, then one exact side test.
+  // theta: estimate, then one side test.
   int nt, np;
   {
     float tt;
@@ -311,11 +443,13 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
       s = FF{e.sh, e.sl};
     } else {
       bool cn, sn;
-      sincospi_grid(2 * k + 1 - F.N, F.Dt, tab_t, F.Kt_h, F.Kt_l, c, s, cn, sn);
+      sincospi_grid(2 * k + 1 - F.N, F.Dt, tab_t, F.st, F.Kt_h, F.Kt_l, c, s, cn, sn);
       c = neg_if(c, cn);
       s = neg_if(s, sn);
     }
-    nt = k + (side_ge(ys, 0.0f, c, xs, s) ? 1 : 0);
+    int side = side_ge(ys, 0.0f, c, xs, s);
+    if (side < 0) side = side_theta_f64<MAP>(xs, ys, k, F);
+    nt = k + side;
   }
   // phi: rho = sqrt(x^2 + y^2) in double-float.
   {
@@ -343,10 +477,12 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
       s = FF{e.sh, e.sl};
     } else {
       bool cn, sn;
-      sincospi_grid(2 * k + 1, F.Dp, tab_p, F.Kp_h, F.Kp_l, c, s, cn, sn);
+      sincospi_grid(2 * k + 1, F.Dp, tab_p, F.sp, F.Kp_h, F.Kp_l, c, s, cn, sn);
       c = neg_if(c, cn);
     }
-    np = k + (side_ge(rho_h, rho_l, c, zs, s) ? 1 : 0);
+    int side = side_ge(rho_h, rho_l, c, zs, s);
+    if (side < 0) side = side_phi_f64<MAP>(xs, ys, zs, k, F);
+    np = k + side;
   }
   if (nt == F.N) nt = 0;
   if (np == 0 || np == F.M) nt = 0;

@@ -1,0 +1,440 @@
+// Fast path for the paper's primary layout <0,7,22>-17-18, b7 = 80 (Sec. 3,
+// Sec. 5), uniform map, default range handling.  Same results as the generic
+// path in ivc_device.cuh (shared tables, same error bounds, same FP64
+// fallbacks); organised for GB300 issue throughput:
+//   * every thread carries two vectors and does their FP32 arithmetic with the
+//     packed f32x2 instructions (__ffma2 / __fadd2 / __fmul2, sm_100+);
+//   * field extraction, the exact angle folds and table addressing use float
+//     arithmetic on exact small integers and magic-number rounding, keeping
+//     the integer/compare pipe for the few decisions that need it;
+//   * encoding estimates t with an octant-reduced atan polynomial (error about
+//     0.01 bin in t) and runs the error-free side-of-boundary test only for
+//     coordinates within 0.03 bin of a rounding boundary, in a warp loop over
+//     the pending tests;
+//   * vectors outside |x|_inf in [2^-32, 2^32] (zero, NaN, Inf, tiny, huge) and
+//     non-finite words take the generic code, off the common path.
+#pragma once
+#include "ivc_device.cuh"
+
+namespace ivc {
+namespace fast {
+
+constexpr int kN = 262143;          // n_theta_max
+constexpr int kM = 131071;          // n_phi_max
+constexpr int kDt = kN;             // theta grid pi m / N
+constexpr int kDp = 2 * kM;         // phi grid pi m / (2M)
+constexpr int kShift = 8;           // table step 2^8 units (both grids)
+constexpr int kNent = 513;          // entries per grid
+constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;
+constexpr float kEps = 0.03f;       // bin-coordinate estimate error bound (with margin)
+
+// The primary layout is the one this path serves.
+__host__ __device__ inline bool is_primary(const DevFormat &F) {
+  return F.sh_phi == 18 && F.sh_m == 35 && F.sh_e == 57 && F.mask_e == 127u &&
+         F.mask_m == 0x3FFFFFu && F.e_off == -47 && F.N == kN && F.M == kM && F.st == kShift &&
+         F.sp == kShift && F.nent_t == kNent && F.nent_p == kNent && F.under_mode == 0 &&
+         F.over_mode == 0;
+}
+
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }
+__device__ __forceinline__ float2 sel2(bool c0, bool c1, float2 a, float2 b) {
+  return make_float2(c0 ? a.x : b.x, c1 ? a.y : b.y);
+}
+
+struct FF2 {
+  float2 h, l;
+};
+
+// ------------------------------------------------------------ trig (packed)
+
+// Folded angle in [0, pi/4] as pi b / (2D) for both elements, with the role
+// flags of the original angle.
+struct Fold2 {
+  float2 b;
+  bool swap0, swap1, cneg0, cneg1;
+};
+
+// cos/sin magnitudes of pi b / (2D) for both elements from the shared table.
+__device__ __forceinline__ void sincos2(float2 b, const TabEntry *__restrict__ tab, float Kh,
+                                        float Kl, FF2 &c, FF2 &s) {
+  // h = nearest integer to b / 256 (magic-number rounding), l = b - 256 h
+  const float2 hb = fma2(b, bc(1.0f / 256.0f), bc(kMagic));
+  const float2 hf = add2(hb, bc(-kMagic));
+  const float2 lf = fma2(hf, bc(-256.0f), b);
+  const uint32_t i0 = __float_as_uint(hb.x) - kMagicBits;
+  const uint32_t i1 = __float_as_uint(hb.y) - kMagicBits;
+  const TabEntry e0 = tab[i0];
+  const TabEntry e1 = tab[i1];
+  const float2 X = make_float2(e0.ch, e1.ch), Xl = make_float2(e0.cl, e1.cl);
+  const float2 Y = make_float2(e0.sh, e1.sh), Yl = make_float2(e0.sl, e1.sl);
+  const float2 bh = mul2(lf, bc(Kh));
+  const float2 bl = add2(fma2(lf, bc(Kh), neg2(bh)), mul2(lf, bc(Kl)));
+  const float2 b2 = mul2(bh, bh);
+  const float2 u = mul2(b2, fma2(b2, bc(-1.0f / 24.0f), bc(0.5f)));
+  const float2 st = fma2(mul2(bh, b2), fma2(b2, bc(1.0f / 120.0f), bc(-1.0f / 6.0f)), bl);
+  // cos(A + beta) = cA - cA u - sA sin(beta)
+  const float2 P = mul2(Y, bh);
+  const float2 Pe = fma2(Y, bh, neg2(P));
+  const float2 Ch = sub2(X, P);
+  const float2 Ce = sub2(sub2(X, Ch), P);
+  float2 Cl = add2(Ce, Xl);
+  Cl = sub2(Cl, Pe);
+  Cl = fma2(neg2(X), u, Cl);
+  Cl = fma2(neg2(Y), st, Cl);
+  Cl = fma2(neg2(Yl), bh, Cl);
+  // sin(A + beta) = sA - sA u + cA sin(beta)
+  const float2 Q = mul2(X, bh);
+  const float2 Qe = fma2(X, bh, neg2(Q));
+  const float2 Sh = add2(Y, Q);
+  const float2 Se = sub2(Q, sub2(Sh, Y));
+  float2 Sl = add2(Se, Qe);
+  Sl = add2(Sl, Yl);
+  Sl = fma2(neg2(Y), u, Sl);
+  Sl = fma2(X, st, Sl);
+  Sl = fma2(Xl, bh, Sl);
+  c.h = Ch; c.l = Cl;
+  s.h = Sh; s.l = Sl;
+}
+
+// Exact fold of pi m / D, given |m| as exact float a in [0, D].
+__device__ __forceinline__ Fold2 fold2(float2 a, float D) {
+  Fold2 f;
+  const float2 na = fma2(a, bc(-1.0f), bc(D));        // D - a
+  f.cneg0 = a.x > na.x;
+  f.cneg1 = a.y > na.y;
+  const float2 a1 = make_float2(fminf(a.x, na.x), fminf(a.y, na.y));
+  const float2 t2 = add2(a1, a1);
+  const float2 nt2 = fma2(a1, bc(-2.0f), bc(D));      // D - 2 a1
+  f.swap0 = t2.x > nt2.x;
+  f.swap1 = t2.y > nt2.y;
+  f.b = make_float2(fminf(t2.x, nt2.x), fminf(t2.y, nt2.y));
+  return f;
+}
+
+// ----------------------------------------------------------------- decode
+
+// Round-up (away from zero for magnitudes) of (Ph + Pl) with the ambiguity
+// test of the generic path, for both elements.
+__device__ __forceinline__ float2 ru_pair(float2 P, float2 T, bool &amb0, bool &amb1) {
+  const float2 d = mul2(P, bc(kDecodeAmbig));
+  const float2 x0 = __fadd2_ru(P, sub2(T, d));
+  const float2 x1 = __fadd2_ru(P, add2(T, d));
+  amb0 |= (x0.x != x1.x);
+  amb1 |= (x0.y != x1.y);
+  return x1;
+}
+
+// RU(r (a.h + a.l)) with a double-float a: returns (P, T) with P + T the value.
+__device__ __forceinline__ void prod2(float2 r, FF2 a, float2 &P, float2 &T) {
+  P = mul2(r, a.h);
+  const float2 Pe = fma2(r, a.h, neg2(P));
+  T = fma2(r, a.l, Pe);
+}
+
+__device__ __forceinline__ void prod3(FF2 R, FF2 a, float2 &P, float2 &T) {
+  P = mul2(R.h, a.h);
+  const float2 Pe = fma2(R.h, a.h, neg2(P));
+  T = fma2(R.h, a.l, fma2(R.l, a.h, Pe));
+}
+
+__device__ __forceinline__ float apply_neg(float v, bool n) { return (n && v != 0.0f) ? -v : v; }
+
+// Decodes two words; returns false in *ok for an element that needs the
+// generic path (non-finite word or an ambiguous rounding).
+__device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry *__restrict__ tab_t,
+                                        const TabEntry *__restrict__ tab_p, float Kt_h,
+                                        float Kt_l, float Kp_h, float Kp_l, float2 &X,
+                                        float2 &Y, float2 &Z, bool &slow0, bool &slow1) {
+  const uint32_t hi0 = (uint32_t)(w0 >> 32), lo0 = (uint32_t)w0;
+  const uint32_t hi1 = (uint32_t)(w1 >> 32), lo1 = (uint32_t)w1;
+  const uint32_t E0 = hi0 >> 25, E1 = hi1 >> 25;
+  // r^ bits: exponent E7 + 47, mantissa m22 << 1 (Sec. 2.3)
+  const float r0 = E0 == 0u ? 0.0f : __uint_as_float(((hi0 >> 2) & 0xFFFFFFFEu) + (47u << 23));
+  const float r1 = E1 == 0u ? 0.0f : __uint_as_float(((hi1 >> 2) & 0xFFFFFFFEu) + (47u << 23));
+  slow0 = (E0 == 127u);
+  slow1 = (E1 == 127u);
+  // n_theta, n_phi as exact floats (magic-number conversion)
+  const float2 ntf = add2(make_float2(__uint_as_float((lo0 & 0x3FFFFu) | 0x4B000000u),
+                                      __uint_as_float((lo1 & 0x3FFFFu) | 0x4B000000u)),
+                          bc(-8388608.0f));
+  const float2 npf = add2(make_float2(__uint_as_float((__funnelshift_r(lo0, hi0, 18) & 0x1FFFFu) |
+                                                      0x4B000000u),
+                                      __uint_as_float((__funnelshift_r(lo1, hi1, 18) & 0x1FFFFu) |
+                                                      0x4B000000u)),
+                          bc(-8388608.0f));
+  // theta^ = pi (2 n_theta - N) / N
+  const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)kN));
+  const bool sn0 = mt.x < 0.0f, sn1 = mt.y < 0.0f;
+  const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)kDt);
+  FF2 cc, ss;
+  sincos2(ft.b, tab_t, Kt_h, Kt_l, cc, ss);
+  FF2 ct, st;
+  ct.h = sel2(ft.swap0, ft.swap1, ss.h, cc.h);
+  ct.l = sel2(ft.swap0, ft.swap1, ss.l, cc.l);
+  st.h = sel2(ft.swap0, ft.swap1, cc.h, ss.h);
+  st.l = sel2(ft.swap0, ft.swap1, cc.l, ss.l);
+  // phi^ = pi (2 n_phi) / (2M)
+  const Fold2 fp = fold2(add2(npf, npf), (float)kDp);
+  sincos2(fp.b, tab_p, Kp_h, Kp_l, cc, ss);
+  FF2 cp, sp;
+  cp.h = sel2(fp.swap0, fp.swap1, ss.h, cc.h);
+  cp.l = sel2(fp.swap0, fp.swap1, ss.l, cc.l);
+  sp.h = sel2(fp.swap0, fp.swap1, cc.h, ss.h);
+  sp.l = sel2(fp.swap0, fp.swap1, cc.l, ss.l);
+  // x = r cos(theta) sin(phi), y = r sin(theta) sin(phi), z = r cos(phi)
+  const float2 r = make_float2(r0, r1);
+  FF2 R;
+  prod2(r, sp, R.h, R.l);
+  float2 P, T;
+  bool a0 = false, a1 = false;
+  prod3(R, ct, P, T);
+  const float2 x = ru_pair(P, T, a0, a1);
+  prod3(R, st, P, T);
+  const float2 y = ru_pair(P, T, a0, a1);
+  prod2(r, cp, P, T);
+  const float2 z = ru_pair(P, T, a0, a1);
+  slow0 |= a0;
+  slow1 |= a1;
+  X = make_float2(apply_neg(x.x, ft.cneg0), apply_neg(x.y, ft.cneg1));
+  Y = make_float2(apply_neg(y.x, sn0), apply_neg(y.y, sn1));
+  Z = make_float2(apply_neg(z.x, fp.cneg0), apply_neg(z.y, fp.cneg1));
+}
+
+// ----------------------------------------------------------------- encode
+
+// atan(q) for q in [0, 1], degree-15 odd polynomial (max error 4e-8; 1.4e-7
+// in FP32 evaluation).
+__device__ __forceinline__ float2 atan01(float2 q) {
+  const float2 q2 = mul2(q, q);
+  float2 p = bc(-0.0040540566f);
+  p = fma2(p, q2, bc(0.021872252f));
+  p = fma2(p, q2, bc(-0.055908315f));
+  p = fma2(p, q2, bc(0.096313581f));
+  p = fma2(p, q2, bc(-0.13918079f));
+  p = fma2(p, q2, bc(0.19953185f));
+  p = fma2(p, q2, bc(-0.33331448f));
+  p = fma2(p, q2, bc(0.99999958f));
+  return mul2(p, q);
+}
+
+// Both bin coordinates of two vectors: floor of t (as float) and frac(t).
+struct Est2 {
+  float2 fl_t, fr_t;   // theta: t = 131071 + h, h = w + 1/2
+  float2 fl_p, fr_p;   // phi:   t directly
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r2h) {
+  Est2 e;
+  // theta = atan2(y, x): octant reduction, t = N/2 + w, w = N theta / (2 pi)
+  {
+    const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
+    const float mx0 = fmaxf(ax0, ay0), mn0 = fminf(ax0, ay0);
+    const float mx1 = fmaxf(ax1, ay1), mn1 = fminf(ax1, ay1);
+    const float2 q = make_float2(fminf(mn0 * rcp_approx(mx0), 1.0f), fminf(mn1 * rcp_approx(mx1), 1.0f));
+    const float2 g = mul2(atan01(q), bc((float)(kN / 6.283185307179586)));
+    const float2 gq = fma2(g, bc(-1.0f), bc(0.25f * (float)kN));       // N/4 - g
+    const float2 u = sel2(ay0 > ax0, ay1 > ax1, gq, g);
+    const float2 uv = fma2(u, bc(-1.0f), bc(0.5f * (float)kN));        // N/2 - u
+    const float2 v = sel2(x.x < 0.0f, x.y < 0.0f, uv, u);
+    const float2 w = make_float2(copysignf(v.x, y.x), copysignf(v.y, y.y));
+    // t = 131071 + h, clamped to [0, N - 1/4] like the generic path
+    float2 h = add2(w, bc(0.5f));
+    h = make_float2(fminf(fmaxf(h.x, -131071.0f), 131071.75f),
+                    fminf(fmaxf(h.y, -131071.0f), 131071.75f));
+    const float2 m = __fadd2_rd(h, bc(kMagic));
+    e.fl_t = add2(m, bc(-kMagic));
+    e.fr_t = sub2(h, e.fl_t);
+  }
+  // phi = atan2(rho, z), t = M phi / pi
+  {
+    const float rho0 = sqrt_approx(r2h.x), rho1 = sqrt_approx(r2h.y);
+    const float az0 = fabsf(z.x), az1 = fabsf(z.y);
+    const float mx0 = fmaxf(az0, rho0), mn0 = fminf(az0, rho0);
+    const float mx1 = fmaxf(az1, rho1), mn1 = fminf(az1, rho1);
+    const float2 q = make_float2(fminf(mn0 * rcp_approx(mx0), 1.0f), fminf(mn1 * rcp_approx(mx1), 1.0f));
+    const float2 g = mul2(atan01(q), bc((float)(kM / 3.141592653589793)));
+    const float2 gq = fma2(g, bc(-1.0f), bc(0.5f * (float)kM));        // M/2 - g
+    const float2 u = sel2(rho0 > az0, rho1 > az1, gq, g);
+    const float2 um = fma2(u, bc(-1.0f), bc((float)kM));               // M - u
+    float2 t = sel2(z.x < 0.0f, z.y < 0.0f, um, u);
+    t = make_float2(fminf(fmaxf(t.x, 0.0f), (float)kM - 0.25f),
+                    fminf(fmaxf(t.y, 0.0f), (float)kM - 0.25f));
+    const float2 m = __fadd2_rd(t, bc(kMagic));
+    e.fl_p = add2(m, bc(-kMagic));
+    e.fr_p = sub2(t, e.fl_p);
+  }
+  return e;
+}
+
+// Error-free side test for one pending decision (generic tables and FP64
+// fallback).  kind 0: theta boundary k + 1/2; kind 1: phi boundary k + 1/2.
+static __device__ __noinline__ int exact_side(int kind, int k, float xs, float ys, float zs,
+                                       const DevFormat &F, const TabEntry *tab_t,
+                                       const TabEntry *tab_p) {
+  FF c, s;
+  bool cn, sn;
+  if (kind == 0) {
+    sincospi_grid(2 * k + 1 - F.N, F.Dt, tab_t, F.st, F.Kt_h, F.Kt_l, c, s, cn, sn);
+    c = neg_if(c, cn);
+    s = neg_if(s, sn);
+    const int side = side_ge(ys, 0.0f, c, xs, s);
+    return side >= 0 ? side : side_theta_f64<MAP_UNIFORM>(xs, ys, k, F);
+  }
+  sincospi_grid(2 * k + 1, F.Dp, tab_p, F.sp, F.Kp_h, F.Kp_l, c, s, cn, sn);
+  c = neg_if(c, cn);
+  float r2h, r2l;
+  {
+    const float px = xs * xs, ex = fmaf(xs, xs, -px);
+    const float py = ys * ys, ey = fmaf(ys, ys, -py);
+    r2h = px + py;
+    const float t = r2h - px;
+    r2l = ((px - (r2h - t)) + (py - t)) + (ex + ey);
+  }
+  float rho_h = 0.0f, rho_l = 0.0f;
+  if (r2h > 0.0f) {
+    const float y1 = rsqrtf(r2h);
+    const float hy1 = 0.5f * y1;
+    const float q0 = r2h * y1;
+    rho_h = fmaf(fmaf(-q0, q0, r2h) + r2l, hy1, q0);
+    rho_l = (fmaf(-rho_h, rho_h, r2h) + r2l) * hy1;
+  }
+  const int side = side_ge(rho_h, rho_l, c, zs, s);
+  return side >= 0 ? side : side_phi_f64<MAP_UNIFORM>(xs, ys, zs, k, F);
+}
+
+static __device__ __noinline__ uint64_t encode_generic(float x, float y, float z, const DevFormat &F,
+                                                const TabEntry *tab_t, const TabEntry *tab_p) {
+  uint32_t flags = 0;
+  return encode_vec<MAP_UNIFORM>(x, y, z, F, tab_t, tab_p, flags);
+}
+
+static __device__ __noinline__ float3 decode_generic(uint64_t w, const DevFormat &F, const TabEntry *tab_t,
+                                              const TabEntry *tab_p) {
+  return decode_word<MAP_UNIFORM>(w, F, tab_t, tab_p);
+}
+
+// Encodes two vectors.  All lanes of the warp must call it (warp loop).
+__device__ __forceinline__ void encode2(float2 x, float2 y, float2 z, const DevFormat &F,
+                                        const TabEntry *__restrict__ tab_t,
+                                        const TabEntry *__restrict__ tab_p, uint64_t &w0,
+                                        uint64_t &w1) {
+  // |x|_inf in [2^-32, 2^32): no scaling, no range limits, no specials
+  // (integer max of the magnitude bits: NaN compares above every finite value)
+  const uint32_t am0 = max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(y.x) & 0x7fffffffu),
+                           __float_as_uint(z.x) & 0x7fffffffu);
+  const uint32_t am1 = max(max(__float_as_uint(x.y) & 0x7fffffffu, __float_as_uint(y.y) & 0x7fffffffu),
+                           __float_as_uint(z.y) & 0x7fffffffu);
+  const bool gen0 = !((am0 - 0x2F800000u) < 0x20000000u);
+  const bool gen1 = !((am1 - 0x2F800000u) < 0x20000000u);
+  // squares and sums in double-float
+  const float2 px = mul2(x, x), ex = fma2(x, x, neg2(px));
+  const float2 py = mul2(y, y), ey = fma2(y, y, neg2(py));
+  const float2 pz = mul2(z, z), ez = fma2(z, z, neg2(pz));
+  const float2 r2h = add2(px, py);
+  float2 t = sub2(r2h, px);
+  const float2 r2l = add2(add2(sub2(px, sub2(r2h, t)), sub2(py, t)), add2(ex, ey));
+  const float2 sh = add2(r2h, pz);
+  t = sub2(sh, r2h);
+  const float2 sl = add2(add2(sub2(r2h, sub2(sh, t)), sub2(pz, t)), add2(r2l, ez));
+  // double-float square root, RN32
+  const float2 y0 = make_float2(rsqrtf(sh.x), rsqrtf(sh.y));
+  const float2 hy0 = mul2(y0, bc(0.5f));
+  const float2 q0 = mul2(sh, y0);
+  const float2 rh = fma2(add2(fma2(neg2(q0), q0, sh), sl), hy0, q0);
+  const float2 rl = mul2(add2(fma2(neg2(rh), rh, sh), sl), hy0);
+  float2 r32 = add2(rh, rl);
+  const float2 dev = add2(sub2(rh, r32), rl);
+  bool nslow0, nslow1;
+  {
+    const float hu0 = __uint_as_float((__float_as_uint(r32.x) & 0x7f800000u) - (24u << 23));
+    const float hu1 = __uint_as_float((__float_as_uint(r32.y) & 0x7f800000u) - (24u << 23));
+    nslow0 = (hu0 - fabsf(dev.x) <= kNormAmbig * r32.x) || ((__float_as_uint(r32.x) & 0x7fffffu) == 0u);
+    nslow1 = (hu1 - fabsf(dev.y) <= kNormAmbig * r32.y) || ((__float_as_uint(r32.y) & 0x7fffffu) == 0u);
+  }
+  if (nslow0 && !gen0) r32.x = norm_rn_f64(x.x, y.x, z.x);
+  if (nslow1 && !gen1) r32.y = norm_rn_f64(x.y, y.y, z.y);
+  // angle estimates
+  const Est2 e = estimate2(x, y, z, r2h);
+  int kt0 = 131071 + (int)(__float_as_uint(e.fl_t.x + kMagic) - kMagicBits);
+  int kt1 = 131071 + (int)(__float_as_uint(e.fl_t.y + kMagic) - kMagicBits);
+  int kp0 = (int)(__float_as_uint(e.fl_p.x + kMagic) - kMagicBits);
+  int kp1 = (int)(__float_as_uint(e.fl_p.y + kMagic) - kMagicBits);
+  kt0 = min(max(kt0, 0), kN - 1);
+  kt1 = min(max(kt1, 0), kN - 1);
+  kp0 = min(max(kp0, 0), kM - 1);
+  kp1 = min(max(kp1, 0), kM - 1);
+  int nt0 = kt0 + (e.fr_t.x >= 0.5f ? 1 : 0), nt1 = kt1 + (e.fr_t.y >= 0.5f ? 1 : 0);
+  int np0 = kp0 + (e.fr_p.x >= 0.5f ? 1 : 0), np1 = kp1 + (e.fr_p.y >= 0.5f ? 1 : 0);
+  // pending exact decisions (bit 0/1: element 0 theta/phi, bit 2/3: element 1)
+  uint32_t pend = 0;
+  if (!gen0) {
+    pend |= (fabsf(e.fr_t.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(e.fr_p.x - 0.5f) <= kEps ? 2u : 0u);
+  }
+  if (!gen1) {
+    pend |= (fabsf(e.fr_t.y - 0.5f) <= kEps ? 4u : 0u) | (fabsf(e.fr_p.y - 0.5f) <= kEps ? 8u : 0u);
+  }
+  while (__any_sync(0xffffffffu, pend != 0u)) {
+    if (pend) {
+      const int j = __ffs(pend) - 1;
+      pend &= pend - 1u;
+      const bool el = j >= 2;
+      const int kind = j & 1;
+      const int k = kind ? (el ? kp1 : kp0) : (el ? kt1 : kt0);
+      const int side = exact_side(kind, k, el ? x.y : x.x, el ? y.y : y.x, el ? z.y : z.x, F,
+                                  tab_t, tab_p);
+      if (j == 0) nt0 = kt0 + side;
+      else if (j == 1) np0 = kp0 + side;
+      else if (j == 2) nt1 = kt1 + side;
+      else np1 = kp1 + side;
+    }
+  }
+  // canonical forms and packing (Fig. manbit)
+  if (nt0 == kN || np0 == 0 || np0 == kM) nt0 = 0;
+  if (nt1 == kN || np1 == 0 || np1 == kM) nt1 = 0;
+  const uint32_t rb0 = __float_as_uint(r32.x), rb1 = __float_as_uint(r32.y);
+  const uint32_t hi0 = (((rb0 - (47u << 23)) << 2) & 0xFFFFFFF8u) | ((uint32_t)np0 >> 14);
+  const uint32_t hi1 = (((rb1 - (47u << 23)) << 2) & 0xFFFFFFF8u) | ((uint32_t)np1 >> 14);
+  const uint32_t lo0 = ((uint32_t)np0 << 18) | (uint32_t)nt0;
+  const uint32_t lo1 = ((uint32_t)np1 << 18) | (uint32_t)nt1;
+  w0 = ((uint64_t)hi0 << 32) | lo0;
+  w1 = ((uint64_t)hi1 << 32) | lo1;
+  if (gen0) w0 = encode_generic(x.x, y.x, z.x, F, tab_t, tab_p);
+  if (gen1) w1 = encode_generic(x.y, y.y, z.y, F, tab_t, tab_p);
+}
+
+// Decodes two words through the fast path, falling back per element.
+__device__ __forceinline__ void decode2_full(uint64_t w0, uint64_t w1, const DevFormat &F,
+                                             const TabEntry *tab_t, const TabEntry *tab_p,
+                                             float2 &X, float2 &Y, float2 &Z) {
+  bool s0, s1;
+  decode2(w0, w1, tab_t, tab_p, F.Kt_h, F.Kt_l, F.Kp_h, F.Kp_l, X, Y, Z, s0, s1);
+  if (s0) {
+    const float3 v = decode_generic(w0, F, tab_t, tab_p);
+    X.x = v.x; Y.x = v.y; Z.x = v.z;
+  }
+  if (s1) {
+    const float3 v = decode_generic(w1, F, tab_t, tab_p);
+    X.y = v.x; Y.y = v.y; Z.y = v.z;
+  }
+}
+
+}  // namespace fast
+}  // namespace ivc

@@ -7,6 +7,7 @@
 
 #include "../../include/ivc.h"
 #include "ivc_device.cuh"
+#include "ivc_fast.cuh"
 
 namespace ivc {
 
@@ -18,6 +19,11 @@ enum KernelKind : int {
   K_UPDATE = 4,
   K_BATCH_ADD = 5,
   K_BATCH_AXPY = 6,
+  K_ADD_FAST = 7,
+  K_AXPY_FAST = 8,
+  K_UPDATE_FAST = 9,
+  K_BATCH_ADD_FAST = 10,
+  K_BATCH_AXPY_FAST = 11,
 };
 
 struct LaunchShape {
@@ -63,6 +69,15 @@ cudaError_t launch_axpy(int map, const DevFormat &F, float alpha, const uint64_t
 cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t *v,
                           const uint64_t *f, const float *rho, uint64_t *v_out, uint64_t *m_out,
                           int64_t n, const LaunchShape &s, cudaStream_t st);
+// Fast path of the primary layout (requires fast::is_primary(F)); two words
+// per thread, n >= 0, 16-byte aligned word arrays.
+cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_t *b, uint64_t *c,
+                            int64_t n, const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
+                             int64_t n, const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, const uint64_t *f,
+                               const float *rho, uint64_t *v_out, uint64_t *m_out, int64_t n,
+                               const LaunchShape &s, cudaStream_t st);
 cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P,
                            const LaunchShape &s, cudaStream_t st);
 cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,

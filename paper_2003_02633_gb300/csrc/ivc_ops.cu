@@ -187,6 +187,116 @@ __global__ void __launch_bounds__(256) k_update(const __grid_constant__ DevForma
   }
 }
 
+
+// ------------------------------------------------------------- fast path
+// Primary layout, two vectors per thread, packed FP32x2 arithmetic.  The loop
+// trip count is uniform per warp (the encode's exact-test loop votes across
+// the warp); lanes past the end work on zero words and store nothing.
+
+// out[i] = encode(op(decode(a[i]), decode(b[i]))) for i in [0, n) by the
+// calling threads: warp `warp` of `nwarps` takes word pairs warp*32 + lane,
+// (warp + nwarps)*32 + lane, ...; the trip count is uniform per warp.  The odd
+// tail element goes to the thread with warp == 0 and lane == 0.
+template <int OP>
+__device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64_t *b, uint64_t *c,
+                                                 int64_t n, int64_t warp, int64_t nwarps, int lane,
+                                                 float alpha, const DevFormat &F,
+                                                 const TabEntry *tab_t, const TabEntry *tab_p) {
+  const int64_t n2 = n >> 1;
+  const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(a);
+  const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(b);
+  ulonglong2 *c2 = reinterpret_cast<ulonglong2 *>(c);
+  for (int64_t base = warp * 32; base < n2; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    const bool act = i < n2;
+    const ulonglong2 wa = act ? __ldcs(a2 + i) : make_ulonglong2(0ull, 0ull);
+    const ulonglong2 wb = act ? __ldcs(b2 + i) : make_ulonglong2(0ull, 0ull);
+    float2 ux, uy, uz, vx, vy, vz;
+    fast::decode2_full(wa.x, wa.y, F, tab_t, tab_p, ux, uy, uz);
+    fast::decode2_full(wb.x, wb.y, F, tab_t, tab_p, vx, vy, vz);
+    float2 sx, sy, sz;
+    if (OP == IVC_OP_ADD) {
+      sx = fast::add2(ux, vx); sy = fast::add2(uy, vy); sz = fast::add2(uz, vz);
+    } else {
+      sx = fast::fma2(fast::bc(alpha), ux, vx);
+      sy = fast::fma2(fast::bc(alpha), uy, vy);
+      sz = fast::fma2(fast::bc(alpha), uz, vz);
+    }
+    uint64_t w0, w1;
+    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1);
+    if (act) __stcs(c2 + i, make_ulonglong2(w0, w1));
+  }
+  if ((n & 1) && warp == 0 && lane == 0) {
+    uint32_t flags = 0;
+    const int64_t i = n - 1;
+    if (OP == IVC_OP_ADD)
+      c[i] = fused1<MAP_UNIFORM>(a[i], b[i], OpAdd{}, F, tab_t, tab_p, flags);
+    else
+      c[i] = fused1<MAP_UNIFORM>(a[i], b[i], OpAxpy{alpha}, F, tab_t, tab_p, flags);
+  }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_fused_fast(const __grid_constant__ DevFormat F,
+                                                    const uint64_t *a, const uint64_t *b,
+                                                    uint64_t *c, int64_t n, float alpha) {
+  IVC_TABLES(F, MAP_UNIFORM);
+  fused_fast_range<OP>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                       ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t,
+                       tab_p);
+}
+
+// v_out = encode(fmaf(dt, f, v)); m_out = encode(rho * v_new) (if requested).
+__global__ void __launch_bounds__(256) k_update_fast(const __grid_constant__ DevFormat F, float dt,
+                                                     const uint64_t *v, const uint64_t *f,
+                                                     const float *__restrict__ rho,
+                                                     uint64_t *v_out, uint64_t *m_out, int64_t n) {
+  IVC_TABLES(F, MAP_UNIFORM);
+  const bool want_m = (rho != nullptr) && (m_out != nullptr);
+  const int64_t n2 = n >> 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const ulonglong2 *v2 = reinterpret_cast<const ulonglong2 *>(v);
+  const ulonglong2 *f2 = reinterpret_cast<const ulonglong2 *>(f);
+  ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(v_out);
+  ulonglong2 *m2 = reinterpret_cast<ulonglong2 *>(m_out);
+  for (int64_t base = warp * 32; base < n2; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    const bool act = i < n2;
+    const ulonglong2 wv = act ? __ldcs(v2 + i) : make_ulonglong2(0ull, 0ull);
+    const ulonglong2 wf = act ? __ldcs(f2 + i) : make_ulonglong2(0ull, 0ull);
+    float2 ux, uy, uz, gx, gy, gz;
+    fast::decode2_full(wv.x, wv.y, F, tab_t, tab_p, ux, uy, uz);
+    fast::decode2_full(wf.x, wf.y, F, tab_t, tab_p, gx, gy, gz);
+    const float2 sx = fast::fma2(fast::bc(dt), gx, ux);
+    const float2 sy = fast::fma2(fast::bc(dt), gy, uy);
+    const float2 sz = fast::fma2(fast::bc(dt), gz, uz);
+    uint64_t w0, w1;
+    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1);
+    if (act) __stcs(o2 + i, make_ulonglong2(w0, w1));
+    if (want_m) {
+      const float2 q = act ? make_float2(__ldcs(rho + 2 * i), __ldcs(rho + 2 * i + 1))
+                           : make_float2(0.0f, 0.0f);
+      fast::encode2(fast::mul2(q, sx), fast::mul2(q, sy), fast::mul2(q, sz), F, tab_t, tab_p, w0,
+                    w1);
+      if (act) __stcs(m2 + i, make_ulonglong2(w0, w1));
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    uint32_t flags = 0;
+    const int64_t i = n - 1;
+    const float3 vv = decode_word<MAP_UNIFORM>(v[i], F, tab_t, tab_p);
+    const float3 ff = decode_word<MAP_UNIFORM>(f[i], F, tab_t, tab_p);
+    const float sx = fmaf(dt, ff.x, vv.x), sy = fmaf(dt, ff.y, vv.y), sz = fmaf(dt, ff.z, vv.z);
+    v_out[i] = encode_vec<MAP_UNIFORM>(sx, sy, sz, F, tab_t, tab_p, flags);
+    if (want_m) {
+      const float q = rho[i];
+      m_out[i] = encode_vec<MAP_UNIFORM>(q * sx, q * sy, q * sz, F, tab_t, tab_p, flags);
+    }
+  }
+}
+
 // ------------------------------------------------------------------- batched
 
 // Persistent kernel: blocks pull tiles from a device counter; the loop is
@@ -228,6 +338,51 @@ __global__ void __launch_bounds__(256) k_batched(const __grid_constant__ DevForm
     else
       fused_range<MAP>(a, b, c, len, vec2, threadIdx.x, blockDim.x, OpAxpy{fd.alpha}, F, tab_t,
                        tab_p, flags);
+  }
+  if (!done && threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_TIMEOUT);
+}
+
+// Batched persistent kernel on the primary-layout fast path (tiles of an
+// even number of words; 16-byte aligned fields use the packed loop).
+template <int OP>
+__global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ DevFormat F,
+                                                      const __grid_constant__ PlanDev P) {
+  IVC_TABLES(F, MAP_UNIFORM);
+  __shared__ long long s_tile;
+  uint32_t flags = 0;
+  bool done = false;
+  for (int64_t iter = 0; iter <= P.total_tiles; ++iter) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(P.counter, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    __syncthreads();
+    if (tile >= P.total_tiles) {
+      done = true;
+      break;
+    }
+    int lo = 0, hi = P.nfields;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (P.tile_start[mid] <= tile) lo = mid; else hi = mid;
+    }
+    const FieldDesc fd = P.fields[lo];
+    const int64_t start = (tile - P.tile_start[lo]) * (int64_t)P.tile;
+    const int64_t len = min((int64_t)P.tile, fd.n - start);
+    const uint64_t *a = fd.a + start;
+    const uint64_t *b = (OP == IVC_OP_ADD ? fd.b : fd.c) + start;
+    uint64_t *c = fd.c + start;
+    const bool vec2 = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+                        reinterpret_cast<uintptr_t>(c)) & 15u) == 0;
+    if (vec2) {
+      fused_fast_range<OP>(a, b, c, len, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31,
+                           fd.alpha, F, tab_t, tab_p);
+    } else if (OP == IVC_OP_ADD) {
+      fused_range<MAP_UNIFORM>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAdd{}, F, tab_t,
+                               tab_p, flags);
+    } else {
+      fused_range<MAP_UNIFORM>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAxpy{fd.alpha}, F,
+                               tab_t, tab_p, flags);
+    }
   }
   if (!done && threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_TIMEOUT);
 }
@@ -289,6 +444,13 @@ cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t 
 
 cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P,
                            const LaunchShape &s, cudaStream_t st) {
+  if (map == MAP_UNIFORM && fast::is_primary(F)) {
+    if (op == IVC_OP_ADD)
+      k_batched_fast<IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, P);
+    else
+      k_batched_fast<IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, P);
+    return cudaGetLastError();
+  }
   if (op == IVC_OP_ADD) {
     switch (map) {
       case MAP_UNIFORM: k_batched<MAP_UNIFORM, IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, P); break;
@@ -302,6 +464,25 @@ cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P
       default: k_batched<MAP_FRACSPLIT, IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, P); break;
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_t *b, uint64_t *c,
+                            int64_t n, const LaunchShape &s, cudaStream_t st) {
+  k_fused_fast<IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n, 0.0f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
+                             int64_t n, const LaunchShape &s, cudaStream_t st) {
+  k_fused_fast<IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, const uint64_t *f,
+                               const float *rho, uint64_t *v_out, uint64_t *m_out, int64_t n,
+                               const LaunchShape &s, cudaStream_t st) {
+  k_update_fast<<<s.grid, s.block, s.smem, st>>>(F, dt, v, f, rho, v_out, m_out, n);
   return cudaGetLastError();
 }
 
@@ -320,6 +501,11 @@ static const void *kernel_ptr(int kind) {
     case K_AXPY: return (const void *)k_axpy<MAP>;
     case K_UPDATE: return (const void *)k_update<MAP>;
     case K_BATCH_ADD: return (const void *)k_batched<MAP, IVC_OP_ADD>;
+    case K_ADD_FAST: return (const void *)k_fused_fast<IVC_OP_ADD>;
+    case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY>;
+    case K_UPDATE_FAST: return (const void *)k_update_fast;
+    case K_BATCH_ADD_FAST: return (const void *)k_batched_fast<IVC_OP_ADD>;
+    case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY>;
     default: return (const void *)k_batched<MAP, IVC_OP_AXPY>;
   }
 }

@@ -333,3 +333,17 @@ def tune(fmt, op, a, b, c, stream=None) -> ivc_launch_config:
     _chk(load().ivc_tune(ctypes.byref(fmt), op, _ptr(a), _ptr(b), _ptr(c), a.shape[0],
                          _stream(stream), ctypes.byref(best)), "ivc_tune")
     return best
+
+
+_MAX_FIELDS = (3, 5, 7, 9)
+
+
+def merge_stats(parts):
+    """Combine accumulated ivc_error_stats arrays (one per shard or rank):
+    sums add, maxima take the maximum.  Accepts sequences of 11 numbers."""
+    out = [0.0] * IVC_STATS_LEN
+    for p in parts:
+        v = [float(x) for x in p]
+        for k in range(IVC_STATS_LEN):
+            out[k] = max(out[k], v[k]) if k in _MAX_FIELDS else out[k] + v[k]
+    return out

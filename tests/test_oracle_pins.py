@@ -479,3 +479,31 @@ def test_error_stats_definition(oracle_mod):
     assert math.isclose(st["mean"], e.mean(), rel_tol=1e-12)
     assert math.isclose(st["sd"], e.std(ddof=1), rel_tol=1e-9)
     assert math.isclose(st["max"], e.max(), rel_tol=1e-12)
+
+
+@pytest.mark.slow
+def test_tanh_companding_sigma_reduction(oracle_mod):
+    """Sec. 2.5: tanh companding with gamma = 0.5 lowers sigma(e) by about 2%
+    (same sample points, unit sphere)."""
+    O = oracle_mod
+    v = synth.unit_sphere(200000, seed=101)
+    su = O.error_stats(v, O.decompress(O.PRIMARY, O.compress(O.PRIMARY, v)))["sd"]
+    st = O.error_stats(v, O.decompress(O.TANH, O.compress(O.TANH, v)))["sd"]
+    assert -0.03 < st / su - 1 < -0.012
+
+
+def test_fracsplit_sweep_within_figure_window(oracle_mod):
+    """Fig. frac_1718 (N = 1e4 samples): over n_phi_max + 1 in [2^16, 2^18] the
+    mean error stays within the plotted 0.7e-5 .. 1.3e-5 and sigma within
+    0.3e-5 .. 0.7e-5; the split at 2^17 (the plain layout) is the minimum of
+    the mean among the sampled splits."""
+    O = oracle_mod
+    v = synth.unit_sphere(10000, seed=103)
+    means = {}
+    for p1 in (1 << 16, 92682, 1 << 17, 185363, 1 << 18):
+        f = O.Format(map=2, nphi_max_p1=p1)
+        st = O.error_stats(v, O.decompress(f, O.compress(f, v)))
+        assert 0.7e-5 <= st["mean"] <= 1.3e-5, (p1, st["mean"])
+        assert 0.3e-5 <= st["sd"] <= 0.7e-5, (p1, st["sd"])
+        means[p1] = st["mean"]
+    assert min(means, key=means.get) == 1 << 17
