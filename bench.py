@@ -46,6 +46,9 @@ def parse_args():
     p.add_argument("--log2n", type=int, default=28)
     p.add_argument("--no-extra", action="store_true", help="skip the baseline/extra measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--workload", choices=["add", "tgv", "batched", "precision"], default="add",
+                   help="add: the headline line; the others print their own JSON line")
+    p.add_argument("--tgv-elements", type=int, default=96)
     return p.parse_args()
 
 
@@ -431,10 +434,173 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- other workloads
+
+def _gvec(n, ms):
+    return round(n / (ms * 1e-3) / 1e9, 4)
+
+
+def _time_ms(fn, steps, warmup, stream):
+    ms, per = time_launches(fn, steps, warmup, stream)
+    return ms / steps, per
+
+
+def run_tgv(args):
+    """Pointwise update of a TGV velocity field (Sec. 4.2 initial condition) at
+    the 4^3 solution points of each hex of an E^3 mesh: v <- v + dt f with the
+    pressure-gradient forcing, decompress -> update -> recompress, 100 steps;
+    error against the FP64 trajectory, next to the same update on FP32x3."""
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+    dev = torch.device("cuda", 0)
+    fmt = ivc.default_format()
+    E = args.tgv_elements
+    v, f, rho = synth.tgv_fields_device(E, dev)
+    n = v.shape[0]
+    dt = 1e-3
+    nsteps = 100
+    wv, wf = ivc.compress(fmt, v), ivc.compress(fmt, f)
+    wm = torch.empty_like(wv)
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    # FP64 trajectory of the same FP32 inputs
+    exact = v.double() + nsteps * dt * f.double()
+    torch.cuda.synchronize()
+    ms, per = time_launches(lambda: ivc.pointwise_update(fmt, dt, wv, wf, rho=rho, v_out=wv,
+                                                          m_out=wm, stream=s),
+                            nsteps, 0, stream)
+    vc = ivc.decompress(fmt, wv)
+    v32 = v.clone()
+    ms32, _ = time_launches(lambda: ivc.f32_axpy(dt, f, v32, stream=s), nsteps, 0, stream)
+    ex32 = exact.float()
+
+    def err(xh):
+        acc = ivc.error_stats(ex32, xh)
+        d = ivc.stats_dict(acc.cpu())
+        diff = (xh.double() - exact).norm(dim=1)
+        d["max_abs_vs_fp64"] = float(diff.max())
+        d["mean_abs_vs_fp64"] = float(diff.mean())
+        return d
+    line = {"workload": "tgv_pointwise_update", "elements": E, "n_vectors": n, "steps": nsteps,
+            "dt": dt, "ms_per_step": round(ms / nsteps, 5), "gvec_s": _gvec(n, ms / nsteps),
+            "gbs_36B": round(36 * n / (ms / nsteps * 1e-3) / 1e9, 1),
+            "fp32_ms_per_step": round(ms32 / nsteps, 5), "fp32_gvec_s": _gvec(n, ms32 / nsteps),
+            "error_compressed_vs_fp64": err(vc), "error_fp32_vs_fp64": err(v32),
+            "note": "velocity w = 0 makes every initial vector a phi tie (z = 0)"}
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args):
+    """256 fields of uneven length (log-uniform 2^10..2^24), each with its own
+    magnitude window: one persistent launch from a CUDA graph, against 256
+    separate launches and one launch over a single field of the total size."""
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+    dev = torch.device("cuda", 0)
+    fmt = ivc.default_format()
+    lens, win = synth.batched_fields(256, seed=0)
+    fields = []
+    for i, m in enumerate(lens):
+        m = int(m)
+        a = synth.device_vectors(m, 1000 + 2 * i, dev, lo=float(win[i, 0]), hi=float(win[i, 1]))
+        b = synth.device_vectors(m, 1001 + 2 * i, dev, lo=float(win[i, 0]), hi=float(win[i, 1]))
+        fields.append((ivc.compress(fmt, a), ivc.compress(fmt, b),
+                       torch.empty(m, dtype=torch.int64, device=dev), 0.0))
+        del a, b
+    total = int(sum(int(m) for m in lens))
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    steps = max(5, min(args.steps, 50))
+    out = {"workload": "batched_add", "fields": len(fields), "total_vectors": total}
+    for tile in (4096, 16384, 65536):
+        cfg = ivc.ivc_launch_config(256, 2, tile, 0)
+        plan = ivc.BatchedPlan(fmt, ivc.IVC_OP_ADD, fields, cfg=cfg, stream=s)
+        ms, _ = _time_ms(lambda: plan.launch(stream=s), steps, 3, stream)
+        out[f"graph_tile{tile}_gvec_s"] = _gvec(total, ms)
+        ms, _ = _time_ms(lambda: plan.launch(stream=s, graph=False), steps, 3, stream)
+        out[f"direct_tile{tile}_gvec_s"] = _gvec(total, ms)
+        out[f"status_tile{tile}"] = plan.status(stream=s)
+        plan.close()
+
+    def separate():
+        for fa, fb, fc, _ in fields:
+            ivc.add(fmt, fa, fb, out=fc, stream=s)
+    ms, _ = _time_ms(separate, steps, 2, stream)
+    out["separate_launches_gvec_s"] = _gvec(total, ms)
+    big_a = torch.cat([f[0] for f in fields])
+    big_b = torch.cat([f[1] for f in fields])
+    big_c = torch.empty_like(big_a)
+    ms, _ = _time_ms(lambda: ivc.add(fmt, big_a, big_b, out=big_c, stream=s), steps, 3, stream)
+    out["single_field_gvec_s"] = _gvec(total, ms)
+    best = max(v for k, v in out.items() if k.startswith("graph_tile"))
+    out["batched_over_single_field"] = round(best / out["single_field_gvec_s"], 4)
+    print(json.dumps(out), flush=True)
+
+
+def run_precision(args):
+    """Precision sweep: 2^26 vectors with magnitudes 10^U(-30,30), 10 % near the
+    poles, stored as FP32x3, compressed (plain, tanh, fractional split), FP16x3
+    and BF16x3; errors against the FP32 inputs in FP64, range events, and the
+    add throughput of each storage."""
+    import numpy as np
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+    dev = torch.device("cuda", 0)
+    n = 1 << min(args.log2n, 26)
+    x = torch.from_numpy(synth.precision_vectors(n, seed=0)).to(dev)
+    y = torch.from_numpy(synth.precision_vectors(n, seed=1)).to(dev)
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    steps = max(5, min(args.steps, 20))
+    out = {"workload": "precision_sweep", "n_vectors": n}
+
+    def stats(xh):
+        return ivc.stats_dict(ivc.error_stats(x, xh).cpu())
+    out["fp32x3"] = stats(x)
+    for name, kw in (("compressed_plain", {}), ("compressed_tanh", dict(map=1, gamma=0.5)),
+                     ("compressed_fracsplit", dict(map=2, nphi_max_p1=185363))):
+        fmt = ivc.make_format(**kw)
+        counts = torch.zeros(3, dtype=torch.int64, device=dev)
+        w = ivc.compress(fmt, x, counts=counts)
+        d = stats(ivc.decompress(fmt, w))
+        c = counts.cpu().tolist()
+        d.update(n_overflow=c[0], n_underflow=c[1], n_nonfinite=c[2])
+        wy = ivc.compress(fmt, y)
+        wc = torch.empty_like(w)
+        ms, _ = _time_ms(lambda: ivc.add(fmt, w, wy, out=wc, stream=s), steps, 2, stream)
+        d["add_gvec_s"] = _gvec(n, ms)
+        out[name] = d
+    for kind, name in ((ivc.IVC_F16, "fp16x3"), (ivc.IVC_BF16, "bf16x3")):
+        h = ivc.half_from_f32(kind, x)
+        back = ivc.half_to_f32(kind, h)
+        d = stats(back)
+        fin = torch.isfinite(x).all(dim=1)
+        d["n_overflow"] = int((~torch.isfinite(back).all(dim=1) & fin).sum())
+        d["n_underflow"] = int(((back == 0).all(dim=1) & (x != 0).any(dim=1)).sum())
+        hy = ivc.half_from_f32(kind, y)
+        hc = torch.empty_like(h)
+        ms, _ = _time_ms(lambda: ivc.half_add(kind, h, hy, out=hc, stream=s), steps, 2, stream)
+        d["add_gvec_s"] = _gvec(n, ms)
+        out[name] = d
+    c32 = torch.empty_like(x)
+    ms, _ = _time_ms(lambda: ivc.f32_add(x, y, out=c32, stream=s), steps, 2, stream)
+    out["fp32x3"]["add_gvec_s"] = _gvec(n, ms)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "tgv":
+        run_tgv(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ivc(args)
 

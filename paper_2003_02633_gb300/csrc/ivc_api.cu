@@ -191,17 +191,12 @@ ivc_status get_tables(const ivc_format *f, const Geometry &g, int device, TableS
   return IVC_OK;
 }
 
-ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
+}  // namespace
+
+// Fills every field of *F except the table pointers (no device work).
+ivc_status ivc::format_fields(const ivc_format *f, DevFormat *F, int *map_out) {
   Geometry g;
   ivc_status st = geometry(f, &g);
-  if (st != IVC_OK) return st;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return IVC_ERR_CUDA;
-  }
-  TableSet ts;
-  st = get_tables(f, g, dev, &ts);
   if (st != IVC_OK) return st;
   std::memset(F, 0, sizeof(*F));
   F->sh_phi = (uint32_t)f->theta_bits;
@@ -234,7 +229,7 @@ ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
   F->nent_p = table_entries(F->Dp, F->sp);
   ff_split(kPiL / (2.0L * F->Dt), F->Kt_h, F->Kt_l);
   ff_split(kPiL / (2.0L * F->Dp), F->Kp_h, F->Kp_l);
-  F->tab = ts.dev;
+  F->tab = nullptr;
   {
     const unsigned __int128 two64 = (unsigned __int128)1 << 64;
     const unsigned __int128 d = (unsigned __int128)(g.N + 1);
@@ -244,13 +239,34 @@ ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
     F->gam = (float)f->gamma;
     F->tanh_c = (float)tanhl((long double)f->gamma);
     F->tanh_inv2c = (float)(1.0L / (2.0L * tanhl((long double)f->gamma)));
+    F->nent_t = F->nent_p = 0;
+  }
+  *map_out = f->map;
+  return IVC_OK;
+}
+
+namespace {
+
+ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
+  ivc_status st = ivc::format_fields(f, F, map_out);
+  if (st != IVC_OK) return st;
+  Geometry g;
+  geometry(f, &g);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  TableSet ts;
+  st = get_tables(f, g, dev, &ts);
+  if (st != IVC_OK) return st;
+  F->tab = ts.dev;
+  if (f->map == IVC_MAP_TANH) {
     F->dec_t = ts.dev + ts.off_dec_t;
     F->dec_p = ts.dev + ts.off_dec_p;
     F->bnd_t = ts.dev + ts.off_bnd_t;
     F->bnd_p = ts.dev + ts.off_bnd_p;
-    F->nent_t = F->nent_p = 0;
   }
-  *map_out = f->map;
   return IVC_OK;
 }
 
@@ -266,8 +282,10 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
-LaunchShape default_shape(int map, int kind, const DevFormat &F, int64_t n, int vec2,
-                          const ivc_launch_config *cfg) {
+}  // namespace
+
+LaunchShape ivc::default_shape(int map, int kind, const DevFormat &F, int64_t n, int vec2,
+                               const ivc_launch_config *cfg) {
   LaunchShape s;
   s.block = (cfg && cfg->block > 0) ? cfg->block : 256;
   if (s.block > 256) s.block = 256;
@@ -284,6 +302,8 @@ LaunchShape default_shape(int map, int kind, const DevFormat &F, int64_t n, int 
   s.grid = (int)grid;
   return s;
 }
+
+namespace {
 
 ivc_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return IVC_OK;

@@ -27,7 +27,7 @@ constexpr int kShift = 8;           // table step 2^8 units (both grids)
 constexpr int kNent = 513;          // entries per grid
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
-constexpr float kEps = 0.03f;       // bin-coordinate estimate error bound (with margin)
+constexpr float kEps = 0.02f;       // bin-coordinate estimate error bound (with margin)
 
 // The primary layout is the one this path serves.
 __host__ __device__ inline bool is_primary(const DevFormat &F) {
@@ -170,7 +170,6 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry
                           bc(-8388608.0f));
   // theta^ = pi (2 n_theta - N) / N
   const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)kN));
-  const bool sn0 = mt.x < 0.0f, sn1 = mt.y < 0.0f;
   const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)kDt);
   FF2 cc, ss;
   sincos2(ft.b, tab_t, Kt_h, Kt_l, cc, ss);
@@ -201,25 +200,28 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry
   const float2 z = ru_pair(P, T, a0, a1);
   slow0 |= a0;
   slow1 |= a1;
-  X = make_float2(apply_neg(x.x, ft.cneg0), apply_neg(x.y, ft.cneg1));
-  Y = make_float2(apply_neg(y.x, sn0), apply_neg(y.y, sn1));
-  Z = make_float2(apply_neg(z.x, fp.cneg0), apply_neg(z.y, fp.cneg1));
+  // signs: cos(theta^) < 0 iff the fold reflected, sin(theta^) < 0 iff m < 0,
+  // cos(phi^) < 0 iff its fold reflected; (+0) added so that exact zeros are +0
+  X = fma2(x, make_float2(ft.cneg0 ? -1.0f : 1.0f, ft.cneg1 ? -1.0f : 1.0f), bc(0.0f));
+  Y = fma2(y, make_float2(copysignf(1.0f, mt.x), copysignf(1.0f, mt.y)), bc(0.0f));
+  Z = fma2(z, make_float2(fp.cneg0 ? -1.0f : 1.0f, fp.cneg1 ? -1.0f : 1.0f), bc(0.0f));
 }
 
 // ----------------------------------------------------------------- encode
 
-// atan(q) for q in [0, 1], degree-15 odd polynomial (max error 4e-8; 1.4e-7
-// in FP32 evaluation).
+// atan(q) for q in [0, 1]: odd degree-15 polynomial q P(q^2), coefficients
+// from a least-squares-minimax (Lawson) fit on [0, 1]; max error 4e-8 in exact
+// arithmetic, 1.4e-7 rad in FP32 Horner evaluation.
 __device__ __forceinline__ float2 atan01(float2 q) {
   const float2 q2 = mul2(q, q);
-  float2 p = bc(-0.0040540566f);
-  p = fma2(p, q2, bc(0.021872252f));
-  p = fma2(p, q2, bc(-0.055908315f));
-  p = fma2(p, q2, bc(0.096313581f));
-  p = fma2(p, q2, bc(-0.13918079f));
-  p = fma2(p, q2, bc(0.19953185f));
-  p = fma2(p, q2, bc(-0.33331448f));
-  p = fma2(p, q2, bc(0.99999958f));
+  float2 p = bc(-0.004054565913975239f);
+  p = fma2(p, q2, bc(0.021862953901290894f));
+  p = fma2(p, q2, bc(-0.0559123195707798f));
+  p = fma2(p, q2, bc(0.0964219719171524f));
+  p = fma2(p, q2, bc(-0.1390862911939621f));
+  p = fma2(p, q2, bc(0.19946566224098206f));
+  p = fma2(p, q2, bc(-0.33329859375953674f));
+  p = fma2(p, q2, bc(0.9999993443489075f));
   return mul2(p, q);
 }
 
@@ -241,6 +243,15 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
+// min/max in [0, 1] to within an ulp: approximate reciprocal refined by one
+// Newton step; 0/0 (both components zero) gives 1.
+__device__ __forceinline__ float2 quotient(float2 mn, float2 mx) {
+  float2 r = make_float2(rcp_approx(mx.x), rcp_approx(mx.y));
+  r = fma2(r, fma2(neg2(mx), r, bc(1.0f)), r);
+  const float2 q = mul2(mn, r);
+  return make_float2(fminf(q.x, 1.0f), fminf(q.y, 1.0f));
+}
+
 __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r2h) {
   Est2 e;
   // theta = atan2(y, x): octant reduction, t = N/2 + w, w = N theta / (2 pi)
@@ -248,7 +259,7 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
     const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
     const float mx0 = fmaxf(ax0, ay0), mn0 = fminf(ax0, ay0);
     const float mx1 = fmaxf(ax1, ay1), mn1 = fminf(ax1, ay1);
-    const float2 q = make_float2(fminf(mn0 * rcp_approx(mx0), 1.0f), fminf(mn1 * rcp_approx(mx1), 1.0f));
+    const float2 q = quotient(make_float2(mn0, mn1), make_float2(mx0, mx1));
     const float2 g = mul2(atan01(q), bc((float)(kN / 6.283185307179586)));
     const float2 gq = fma2(g, bc(-1.0f), bc(0.25f * (float)kN));       // N/4 - g
     const float2 u = sel2(ay0 > ax0, ay1 > ax1, gq, g);
@@ -269,7 +280,7 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
     const float az0 = fabsf(z.x), az1 = fabsf(z.y);
     const float mx0 = fmaxf(az0, rho0), mn0 = fminf(az0, rho0);
     const float mx1 = fmaxf(az1, rho1), mn1 = fminf(az1, rho1);
-    const float2 q = make_float2(fminf(mn0 * rcp_approx(mx0), 1.0f), fminf(mn1 * rcp_approx(mx1), 1.0f));
+    const float2 q = quotient(make_float2(mn0, mn1), make_float2(mx0, mx1));
     const float2 g = mul2(atan01(q), bc((float)(kM / 3.141592653589793)));
     const float2 gq = fma2(g, bc(-1.0f), bc(0.5f * (float)kM));        // M/2 - g
     const float2 u = sel2(rho0 > az0, rho1 > az1, gq, g);
@@ -286,7 +297,7 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
 
 // Error-free side test for one pending decision (generic tables and FP64
 // fallback).  kind 0: theta boundary k + 1/2; kind 1: phi boundary k + 1/2.
-static __device__ __noinline__ int exact_side(int kind, int k, float xs, float ys, float zs,
+__device__ __forceinline__ int exact_side(int kind, int k, float xs, float ys, float zs,
                                        const DevFormat &F, const TabEntry *tab_t,
                                        const TabEntry *tab_p) {
   FF c, s;

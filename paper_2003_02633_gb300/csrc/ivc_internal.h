@@ -86,4 +86,12 @@ cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int
 // Resident blocks per SM of a kernel at a block size (0 if it cannot run).
 int occupancy(int map, int kind, int block, size_t smem);
 
+// Format fields without table pointers (host only, no device work).
+ivc_status format_fields(const ivc_format *f, DevFormat *F, int *map_out);
+
+// Launch shape: block size from cfg (default 256), grid = SMs x resident
+// blocks (capped by the work), tables in dynamic shared memory.
+LaunchShape default_shape(int map, int kind, const DevFormat &F, int64_t n, int vec2,
+                          const ivc_launch_config *cfg);
+
 }  // namespace ivc

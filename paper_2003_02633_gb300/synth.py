@@ -248,3 +248,32 @@ def random_words(n: int, seed: int = 0, exp_bits: int = 7, man_bits: int = 22,
     sm = np.uint64(theta_bits + phi_bits)
     se = np.uint64(theta_bits + phi_bits + man_bits)
     return (E << se) | (m << sm) | (p << np.uint64(theta_bits)) | t
+
+
+def tgv_fields_device(elements_per_axis: int, device, order: int = 3, p0: float = 100.0,
+                      rho0: float = 1.0, u0: float = 1.0):
+    """``tgv_fields`` evaluated on a torch device (FP64, stored FP32), for mesh
+    sizes where the host version would be slow.  Same point ordering."""
+    import torch
+    q = order + 1
+    xg, _ = np.polynomial.legendre.leggauss(q)
+    E = elements_per_axis
+    h = 2.0 * math.pi / E
+    ecent = -math.pi + h * (torch.arange(E, dtype=torch.float64, device=device) + 0.5)
+    ax = (ecent[:, None] + 0.5 * h * torch.tensor(xg, dtype=torch.float64, device=device)[None, :])
+    shape = (E, E, E, q, q, q)
+    X = ax[None, None, :, None, None, :].expand(shape).reshape(-1)
+    Y = ax[None, :, None, None, :, None].expand(shape).reshape(-1)
+    Z = ax[:, None, None, :, None, None].expand(shape).reshape(-1)
+    u = u0 * torch.sin(X) * torch.cos(Y) * torch.cos(Z)
+    v = -u0 * torch.cos(X) * torch.sin(Y) * torch.cos(Z)
+    w = torch.zeros_like(u)
+    c = rho0 * u0 * u0 / 16.0
+    p = p0 + c * (torch.cos(2 * X) + torch.cos(2 * Y)) * (2 + torch.cos(2 * Z))
+    rho = p * rho0 / p0
+    f = -torch.stack([c * (-2 * torch.sin(2 * X)) * (2 + torch.cos(2 * Z)),
+                      c * (-2 * torch.sin(2 * Y)) * (2 + torch.cos(2 * Z)),
+                      c * (torch.cos(2 * X) + torch.cos(2 * Y)) * (-2 * torch.sin(2 * Z))],
+                     dim=1) / rho[:, None]
+    vel = torch.stack([u, v, w], dim=1)
+    return vel.float().contiguous(), f.float().contiguous(), rho.float().contiguous()
