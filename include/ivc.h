@@ -229,6 +229,24 @@ ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t 
 /* Frees the cached per-format tables on the current device. */
 ivc_status ivc_release_tables(void);
 
+/* Same result as ivc_add, for callers that must not allocate device memory
+ * (for example code running under a framework whose caching allocator owns
+ * the device memory, or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit synchronisation).  There is no counterpart in the
+ * paper: this is a library-level variant of the compressed add.
+ * The tables live in a fixed 32 KiB device array inside the library (held by
+ * every GPU that loads it until exit) instead of cudaMalloc'd memory.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; a call
+ * with a format whose tables are not the ones the array holds rewrites them
+ * first on `stream`.  Calls that overlap on the GPU with different formats
+ * race on the array.  Calls no cudaMalloc/cudaFree.  Errors: as ivc_add, plus
+ * IVC_ERR_UNSUPPORTED for the tanh map and IVC_ERR_NOMEM for a format whose
+ * tables exceed the array (more than 2048 entries). */
+ivc_status ivc_add_noalloc(const ivc_format *fmt, const uint64_t *a, const uint64_t *b,
+                           uint64_t *c, int64_t n, ivc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ _SIGS = {
     "ivc_plan_status": [_P, _P],
     "ivc_plan_destroy": [_P],
     "ivc_tune": [_FMT, _I, _P, _P, _P, _I64, _P, ctypes.POINTER(ivc_launch_config)],
+    "ivc_add_noalloc": [_FMT, _P, _P, _P, _I64, _P],
 }
 EXPORTS = sorted(list(_SIGS) + ["ivc_status_string", "ivc_version"])
 
@@ -193,6 +194,14 @@ def add(fmt, a, b, out=None, cfg=None, stream=None):
     c = ctypes.byref(cfg) if cfg is not None else None
     _chk(load().ivc_add_cfg(ctypes.byref(fmt), _ptr(a), _ptr(b), _ptr(out), a.shape[0], c,
                             _stream(stream)), "ivc_add")
+    return out
+
+
+def add_noalloc(fmt, a, b, out, stream=None):
+    """ivc_add_noalloc: the compressed add with its tables in the library's fixed
+    device array (no device allocation); `out` must be given."""
+    _chk(load().ivc_add_noalloc(ctypes.byref(fmt), _ptr(a), _ptr(b), _ptr(out), a.shape[0],
+                                _stream(stream)), "ivc_add_noalloc")
     return out
 
 
