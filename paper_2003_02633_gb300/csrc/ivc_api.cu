@@ -380,6 +380,11 @@ ivc_status ivc_compress(const ivc_format *fmt, const float *xyz, ivc_layout layo
   if (n == 0) return IVC_OK;
   if (!xyz || !w) return IVC_ERR_ARG;
   if (!aligned(xyz, 4) || !aligned(w, 8) || (counts && !aligned(counts, 8))) return IVC_ERR_ALIGN;
+  if (layout == IVC_AOS && aligned(xyz, 8) && aligned(w, 16) && map == IVC_MAP_UNIFORM &&
+      fast::is_primary(F)) {
+    const LaunchShape s = default_shape(map, K_COMPRESS_FAST, F, n, 1, nullptr);
+    return cuda_status(launch_compress_fast(F, xyz, n, w, counts, s, stream));
+  }
   const LaunchShape s = default_shape(map, K_COMPRESS, F, n, 0, nullptr);
   return cuda_status(launch_compress(map, F, xyz, layout, ld, n, w, counts, s, stream));
 }
@@ -395,6 +400,11 @@ ivc_status ivc_decompress(const ivc_format *fmt, const uint64_t *w, int64_t n, f
   if (n == 0) return IVC_OK;
   if (!xyz || !w) return IVC_ERR_ARG;
   if (!aligned(xyz, 4) || !aligned(w, 8)) return IVC_ERR_ALIGN;
+  if (layout == IVC_AOS && aligned(xyz, 8) && aligned(w, 16) && map == IVC_MAP_UNIFORM &&
+      fast::is_primary(F)) {
+    const LaunchShape s = default_shape(map, K_DECOMPRESS_FAST, F, n, 1, nullptr);
+    return cuda_status(launch_decompress_fast(F, w, n, xyz, s, stream));
+  }
   const LaunchShape s = default_shape(map, K_DECOMPRESS, F, n, 0, nullptr);
   return cuda_status(launch_decompress(map, F, w, n, xyz, layout, ld, s, stream));
 }

@@ -27,7 +27,7 @@ constexpr int kShift = 8;           // table step 2^8 units (both grids)
 constexpr int kNent = 513;          // entries per grid
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
-constexpr float kEps = 0.02f;       // bin-coordinate estimate error bound (with margin)
+constexpr float kEps = 0.005f;      // bin-coordinate estimate error bound (with margin)
 
 // The primary layout is the one this path serves.
 __host__ __device__ inline bool is_primary(const DevFormat &F) {
@@ -209,28 +209,6 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry
 
 // ----------------------------------------------------------------- encode
 
-// atan(q) for q in [0, 1]: odd degree-15 polynomial q P(q^2), coefficients
-// from a least-squares-minimax (Lawson) fit on [0, 1]; max error 4e-8 in exact
-// arithmetic, 1.4e-7 rad in FP32 Horner evaluation.
-__device__ __forceinline__ float2 atan01(float2 q) {
-  const float2 q2 = mul2(q, q);
-  float2 p = bc(-0.004054565913975239f);
-  p = fma2(p, q2, bc(0.021862953901290894f));
-  p = fma2(p, q2, bc(-0.0559123195707798f));
-  p = fma2(p, q2, bc(0.0964219719171524f));
-  p = fma2(p, q2, bc(-0.1390862911939621f));
-  p = fma2(p, q2, bc(0.19946566224098206f));
-  p = fma2(p, q2, bc(-0.33329859375953674f));
-  p = fma2(p, q2, bc(0.9999993443489075f));
-  return mul2(p, q);
-}
-
-// Both bin coordinates of two vectors: floor of t (as float) and frac(t).
-struct Est2 {
-  float2 fl_t, fr_t;   // theta: t = 131071 + h, h = w + 1/2
-  float2 fl_p, fr_p;   // phi:   t directly
-};
-
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -243,97 +221,174 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
-// min/max in [0, 1] to within an ulp: approximate reciprocal refined by one
-// Newton step; 0/0 (both components zero) gives 1.
-__device__ __forceinline__ float2 quotient(float2 mn, float2 mx) {
-  float2 r = make_float2(rcp_approx(mx.x), rcp_approx(mx.y));
-  r = fma2(r, fma2(neg2(mx), r, bc(1.0f)), r);
-  const float2 q = mul2(mn, r);
-  return make_float2(fminf(q.x, 1.0f), fminf(q.y, 1.0f));
+// beta = atan(mn / mx) in [0, pi/4] for 0 <= mn <= mx, as an unevaluated sum
+// bh + bl with |error| < 5e-8 rad:
+//   * q = mn / mx as a double-float qh + ql (Newton-refined reciprocal and the
+//     exact residual mn - mx qh);
+//   * atan(q) = q + q^3 R(q^2), R a degree-7 polynomial from a
+//     least-squares-minimax (Lawson) fit on [0, 1] (7.4e-9 in exact
+//     arithmetic), kept as q + s so that FP32 rounding acts on s only;
+//   * the ql term enters with the slope 1/(1 + q^2), taken as 1 - q^2/2
+//     (ql is below half an ulp of q, so 12 % slope error is negligible).
+// mx = 0 (zero vector in this plane) gives beta = 0.
+__device__ __forceinline__ void atan_ratio2(float2 mn, float2 mx, float2 &bh, float2 &bl) {
+  const float2 m = make_float2(fmaxf(mx.x, 1e-30f), fmaxf(mx.y, 1e-30f));
+  float2 r = make_float2(rcp_approx(m.x), rcp_approx(m.y));
+  r = fma2(r, fma2(neg2(m), r, bc(1.0f)), r);
+  const float2 qh = mul2(mn, r);
+  const float2 ql = mul2(fma2(neg2(m), qh, mn), r);
+  const float2 q2 = mul2(qh, qh);
+  float2 R = bc(0.002622244181111455f);
+  R = fma2(R, q2, bc(-0.015132534317672253f));
+  R = fma2(R, q2, bc(0.04112185537815094f));
+  R = fma2(R, q2, bc(-0.07366705685853958f));
+  R = fma2(R, q2, bc(0.10573931783437729f));
+  R = fma2(R, q2, bc(-0.1418597549200058f));
+  R = fma2(R, q2, bc(0.1999039649963379f));
+  R = fma2(R, q2, bc(-0.33332985639572144f));
+  const float2 sv = mul2(mul2(qh, q2), R);                 // q^3 R(q^2)
+  bh = qh;
+  bl = fma2(ql, fma2(q2, bc(-0.5f), bc(1.0f)), sv);
 }
 
-__device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r2h) {
+// Bin coordinate t = K0 + s1 * C * beta (K0 a multiple of 1/4, s1 = +-1,
+// C = n_max / pi or n_max / (2 pi) in double-float), returned as floor and
+// fraction computed without rounding the large sum: C beta = G + small
+// (exact products and TwoSum), G = Gi + Gf with Gi integral, then
+// t = [K0 + s1 Gi] + s1 (Gf + small).  Error below 0.002 bin.
+struct BinCoord2 {
+  float2 fl, fr;  // floor(t) (exact integer-valued floats) and t - floor(t)
+};
+
+__device__ __forceinline__ float2 floor2(float2 v) {  // |v| < 2^22
+  return add2(__fadd2_rd(v, bc(kMagic)), bc(-kMagic));
+}
+
+__device__ __forceinline__ BinCoord2 bin_coord2(float2 K0, float2 s1, float2 bh, float2 bl, float Ch,
+                                                float Cl) {
+  const float2 p1 = mul2(bc(Ch), bh);
+  const float2 e1 = fma2(bc(Ch), bh, neg2(p1));
+  const float2 p2 = mul2(bc(Ch), bl);
+  const float2 G = add2(p1, p2);                          // TwoSum(p1, p2)
+  const float2 bv = sub2(G, p1);
+  const float2 E2 = add2(sub2(p1, sub2(G, bv)), sub2(p2, bv));
+  const float2 small = fma2(bc(Cl), bh, add2(E2, e1));
+  const float2 Gi = floor2(G);
+  const float2 gfrac = add2(sub2(G, Gi), small);          // in (-0.01, 1.01)
+  const float2 hI = fma2(s1, Gi, K0);                     // exact, quarter-integral
+  const float2 fi = floor2(hI);
+  const float2 f = fma2(s1, gfrac, sub2(hI, fi));         // in (-1.02, 1.77)
+  const float2 fl2 = floor2(f);
+  BinCoord2 c;
+  c.fl = add2(fi, fl2);
+  c.fr = sub2(f, fl2);
+  return c;
+}
+
+struct Est2 {
+  float2 fl_t, fr_t;   // theta: t = 131071 + h, h = w + 1/2 (floor of h, frac)
+  float2 fl_p, fr_p;   // phi:   t directly
+};
+
+__device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r2h, float2 r2l) {
   Est2 e;
-  // theta = atan2(y, x): octant reduction, t = N/2 + w, w = N theta / (2 pi)
+  // theta = atan2(y, x); t = N/2 + w, h = w + 1/2 = K0 + 1/2 + s1 g,
+  // g = N beta / (2 pi), beta = atan(min/max of |x|, |y|)
   {
     const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
-    const float mx0 = fmaxf(ax0, ay0), mn0 = fminf(ax0, ay0);
-    const float mx1 = fmaxf(ax1, ay1), mn1 = fminf(ax1, ay1);
-    const float2 q = quotient(make_float2(mn0, mn1), make_float2(mx0, mx1));
-    const float2 g = mul2(atan01(q), bc((float)(kN / 6.283185307179586)));
-    const float2 gq = fma2(g, bc(-1.0f), bc(0.25f * (float)kN));       // N/4 - g
-    const float2 u = sel2(ay0 > ax0, ay1 > ax1, gq, g);
-    const float2 uv = fma2(u, bc(-1.0f), bc(0.5f * (float)kN));        // N/2 - u
-    const float2 v = sel2(x.x < 0.0f, x.y < 0.0f, uv, u);
-    const float2 w = make_float2(copysignf(v.x, y.x), copysignf(v.y, y.y));
-    // t = 131071 + h, clamped to [0, N - 1/4] like the generic path
-    float2 h = add2(w, bc(0.5f));
-    h = make_float2(fminf(fmaxf(h.x, -131071.0f), 131071.75f),
-                    fminf(fmaxf(h.y, -131071.0f), 131071.75f));
-    const float2 m = __fadd2_rd(h, bc(kMagic));
-    e.fl_t = add2(m, bc(-kMagic));
-    e.fr_t = sub2(h, e.fl_t);
+    float2 bh, bl;
+    atan_ratio2(make_float2(fminf(ax0, ay0), fminf(ax1, ay1)),
+                make_float2(fmaxf(ax0, ay0), fmaxf(ax1, ay1)), bh, bl);
+    // psi = beta (|x| >= |y|) or pi/2 - beta; theta = +-psi (x >= 0) or +-(pi - psi)
+    const bool u0 = ay0 > ax0, u1 = ay1 > ax1;
+    const bool v0 = x.x < 0.0f, v1 = x.y < 0.0f;
+    // u: psi = pi/2 - beta (offset N/4, sign -); v: pi - psi (offset N/2 - ., sign
+    // flips); y < 0 (or -0): theta = -(.) (offset and sign flip)
+    float2 K0 = make_float2(u0 ? 0.25f * (float)kN : 0.0f, u1 ? 0.25f * (float)kN : 0.0f);
+    K0 = make_float2(v0 ? 0.5f * (float)kN - K0.x : K0.x, v1 ? 0.5f * (float)kN - K0.y : K0.y);
+    K0 = make_float2(copysignf(K0.x, y.x), copysignf(K0.y, y.y));
+    // s1 = (u != v ? -1 : 1), negated again for y < 0 (sign-bit xor)
+    const float2 s1 =
+        make_float2(__uint_as_float(__float_as_uint((u0 != v0) ? -1.0f : 1.0f) ^
+                                    (__float_as_uint(y.x) & 0x80000000u)),
+                    __uint_as_float(__float_as_uint((u1 != v1) ? -1.0f : 1.0f) ^
+                                    (__float_as_uint(y.y) & 0x80000000u)));
+    const BinCoord2 c = bin_coord2(add2(K0, bc(0.5f)), s1, bh, bl,
+                                   (float)((double)kN / 6.283185307179586),
+                                   (float)((double)kN / 6.283185307179586 -
+                                           (double)(float)((double)kN / 6.283185307179586)));
+    e.fl_t = c.fl;
+    e.fr_t = c.fr;
   }
-  // phi = atan2(rho, z), t = M phi / pi
+  // phi = atan2(rho, z); t = K0 + s1 g, g = M beta / pi
   {
-    const float rho0 = sqrt_approx(r2h.x), rho1 = sqrt_approx(r2h.y);
+    // rho = sqrt(x^2 + y^2): one Newton step on the double-float sum (relative
+    // error 2^-24, 0.0012 bin); 0 stays about 1e-18
+    const float2 rr = make_float2(fmaxf(r2h.x, 1e-36f), fmaxf(r2h.y, 1e-36f));
+    const float2 yr = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
+    const float2 q0 = mul2(rr, yr);
+    const float2 rho = fma2(add2(fma2(neg2(q0), q0, rr), r2l), mul2(yr, bc(0.5f)), q0);
+    const float rho0 = rho.x, rho1 = rho.y;
     const float az0 = fabsf(z.x), az1 = fabsf(z.y);
-    const float mx0 = fmaxf(az0, rho0), mn0 = fminf(az0, rho0);
-    const float mx1 = fmaxf(az1, rho1), mn1 = fminf(az1, rho1);
-    const float2 q = quotient(make_float2(mn0, mn1), make_float2(mx0, mx1));
-    const float2 g = mul2(atan01(q), bc((float)(kM / 3.141592653589793)));
-    const float2 gq = fma2(g, bc(-1.0f), bc(0.5f * (float)kM));        // M/2 - g
-    const float2 u = sel2(rho0 > az0, rho1 > az1, gq, g);
-    const float2 um = fma2(u, bc(-1.0f), bc((float)kM));               // M - u
-    float2 t = sel2(z.x < 0.0f, z.y < 0.0f, um, u);
-    t = make_float2(fminf(fmaxf(t.x, 0.0f), (float)kM - 0.25f),
-                    fminf(fmaxf(t.y, 0.0f), (float)kM - 0.25f));
-    const float2 m = __fadd2_rd(t, bc(kMagic));
-    e.fl_p = add2(m, bc(-kMagic));
-    e.fr_p = sub2(t, e.fl_p);
+    float2 bh, bl;
+    atan_ratio2(make_float2(fminf(az0, rho0), fminf(az1, rho1)),
+                make_float2(fmaxf(az0, rho0), fmaxf(az1, rho1)), bh, bl);
+    const bool u0 = rho0 > az0, u1 = rho1 > az1;
+    const bool n0 = z.x < 0.0f, n1 = z.y < 0.0f;
+    // |z| >= rho: t = g (z >= 0) or M - g;  rho > |z|: t = M/2 -+ g
+    const float2 K0 = make_float2(u0 ? 0.5f * (float)kM : (n0 ? (float)kM : 0.0f),
+                                  u1 ? 0.5f * (float)kM : (n1 ? (float)kM : 0.0f));
+    const float2 s1 = make_float2((u0 != n0) ? -1.0f : 1.0f, (u1 != n1) ? -1.0f : 1.0f);
+    const BinCoord2 c = bin_coord2(K0, s1, bh, bl, (float)((double)kM / 3.141592653589793),
+                                   (float)((double)kM / 3.141592653589793 -
+                                           (double)(float)((double)kM / 3.141592653589793)));
+    e.fl_p = c.fl;
+    e.fr_p = c.fr;
   }
   return e;
 }
 
 // Error-free side test for one pending decision (generic tables and FP64
-// fallback).  kind 0: theta boundary k + 1/2; kind 1: phi boundary k + 1/2.
+// fallback): kind 0 the theta boundary k + 1/2, kind 1 the phi boundary.
+// One straight path for both kinds.
 __device__ __forceinline__ int exact_side(int kind, int k, float xs, float ys, float zs,
-                                       const DevFormat &F, const TabEntry *tab_t,
-                                       const TabEntry *tab_p) {
+                                          const DevFormat &F, const TabEntry *tab_t,
+                                          const TabEntry *tab_p) {
+  const bool ph = kind != 0;
   FF c, s;
   bool cn, sn;
-  if (kind == 0) {
-    sincospi_grid(2 * k + 1 - F.N, F.Dt, tab_t, F.st, F.Kt_h, F.Kt_l, c, s, cn, sn);
-    c = neg_if(c, cn);
-    s = neg_if(s, sn);
-    const int side = side_ge(ys, 0.0f, c, xs, s);
-    return side >= 0 ? side : side_theta_f64<MAP_UNIFORM>(xs, ys, k, F);
-  }
-  sincospi_grid(2 * k + 1, F.Dp, tab_p, F.sp, F.Kp_h, F.Kp_l, c, s, cn, sn);
+  sincospi_grid(ph ? 2 * k + 1 : 2 * k + 1 - F.N, ph ? F.Dp : F.Dt, ph ? tab_p : tab_t,
+                ph ? F.sp : F.st, ph ? F.Kp_h : F.Kt_h, ph ? F.Kp_l : F.Kt_l, c, s, cn, sn);
   c = neg_if(c, cn);
-  float r2h, r2l;
-  {
+  s = neg_if(s, sn);
+  // theta: sign(y cos - x sin);  phi: sign(rho cos - z sin)
+  float a = ys, a_l = 0.0f;
+  if (ph) {
     const float px = xs * xs, ex = fmaf(xs, xs, -px);
     const float py = ys * ys, ey = fmaf(ys, ys, -py);
-    r2h = px + py;
+    const float r2h = px + py;
     const float t = r2h - px;
-    r2l = ((px - (r2h - t)) + (py - t)) + (ex + ey);
+    const float r2l = ((px - (r2h - t)) + (py - t)) + (ex + ey);
+    float rho_h = 0.0f, rho_l = 0.0f;
+    if (r2h > 0.0f) {
+      const float y1 = rsqrtf(r2h);
+      const float hy1 = 0.5f * y1;
+      const float q0 = r2h * y1;
+      rho_h = fmaf(fmaf(-q0, q0, r2h) + r2l, hy1, q0);
+      rho_l = (fmaf(-rho_h, rho_h, r2h) + r2l) * hy1;
+    }
+    a = rho_h;
+    a_l = rho_l;
   }
-  float rho_h = 0.0f, rho_l = 0.0f;
-  if (r2h > 0.0f) {
-    const float y1 = rsqrtf(r2h);
-    const float hy1 = 0.5f * y1;
-    const float q0 = r2h * y1;
-    rho_h = fmaf(fmaf(-q0, q0, r2h) + r2l, hy1, q0);
-    rho_l = (fmaf(-rho_h, rho_h, r2h) + r2l) * hy1;
-  }
-  const int side = side_ge(rho_h, rho_l, c, zs, s);
-  return side >= 0 ? side : side_phi_f64<MAP_UNIFORM>(xs, ys, zs, k, F);
+  const int side = side_ge(a, a_l, c, ph ? zs : xs, s);
+  if (side >= 0) return side;
+  return ph ? side_phi_f64<MAP_UNIFORM>(xs, ys, zs, k, F)
+            : side_theta_f64<MAP_UNIFORM>(xs, ys, k, F);
 }
 
 static __device__ __noinline__ uint64_t encode_generic(float x, float y, float z, const DevFormat &F,
-                                                const TabEntry *tab_t, const TabEntry *tab_p) {
-  uint32_t flags = 0;
+                                                       const TabEntry *tab_t,
+                                                       const TabEntry *tab_p, uint32_t &flags) {
   return encode_vec<MAP_UNIFORM>(x, y, z, F, tab_t, tab_p, flags);
 }
 
@@ -343,10 +398,12 @@ static __device__ __noinline__ float3 decode_generic(uint64_t w, const DevFormat
 }
 
 // Encodes two vectors.  All lanes of the warp must call it (warp loop).
+// fl0 / fl1 receive the range events of each vector (bit 0 overflow, 1
+// underflow, 2 NaN); only vectors on the generic path can raise them.
 __device__ __forceinline__ void encode2(float2 x, float2 y, float2 z, const DevFormat &F,
                                         const TabEntry *__restrict__ tab_t,
                                         const TabEntry *__restrict__ tab_p, uint64_t &w0,
-                                        uint64_t &w1) {
+                                        uint64_t &w1, uint32_t &fl0, uint32_t &fl1) {
   // |x|_inf in [2^-32, 2^32): no scaling, no range limits, no specials
   // (integer max of the magnitude bits: NaN compares above every finite value)
   const uint32_t am0 = max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(y.x) & 0x7fffffffu),
@@ -383,24 +440,29 @@ __device__ __forceinline__ void encode2(float2 x, float2 y, float2 z, const DevF
   if (nslow0 && !gen0) r32.x = norm_rn_f64(x.x, y.x, z.x);
   if (nslow1 && !gen1) r32.y = norm_rn_f64(x.y, y.y, z.y);
   // angle estimates
-  const Est2 e = estimate2(x, y, z, r2h);
-  int kt0 = 131071 + (int)(__float_as_uint(e.fl_t.x + kMagic) - kMagicBits);
-  int kt1 = 131071 + (int)(__float_as_uint(e.fl_t.y + kMagic) - kMagicBits);
-  int kp0 = (int)(__float_as_uint(e.fl_p.x + kMagic) - kMagicBits);
-  int kp1 = (int)(__float_as_uint(e.fl_p.y + kMagic) - kMagicBits);
-  kt0 = min(max(kt0, 0), kN - 1);
-  kt1 = min(max(kt1, 0), kN - 1);
-  kp0 = min(max(kp0, 0), kM - 1);
-  kp1 = min(max(kp1, 0), kM - 1);
-  int nt0 = kt0 + (e.fr_t.x >= 0.5f ? 1 : 0), nt1 = kt1 + (e.fr_t.y >= 0.5f ? 1 : 0);
-  int np0 = kp0 + (e.fr_p.x >= 0.5f ? 1 : 0), np1 = kp1 + (e.fr_p.y >= 0.5f ? 1 : 0);
+  const Est2 e = estimate2(x, y, z, r2h, r2l);
+  // k = floor(t) clamped to [0, n_max - 1]; the fraction absorbs the clamp
+  // (t = n_max gives fraction 1, t < 0 a negative one: never flagged)
+  float2 ft = add2(e.fl_t, bc(131071.0f));
+  const float2 ftc = make_float2(fminf(fmaxf(ft.x, 0.0f), (float)(kN - 1)),
+                                 fminf(fmaxf(ft.y, 0.0f), (float)(kN - 1)));
+  const float2 frt = add2(e.fr_t, sub2(ft, ftc));
+  const float2 fpc = make_float2(fminf(fmaxf(e.fl_p.x, 0.0f), (float)(kM - 1)),
+                                 fminf(fmaxf(e.fl_p.y, 0.0f), (float)(kM - 1)));
+  const float2 frp = add2(e.fr_p, sub2(e.fl_p, fpc));
+  const int kt0 = (int)(__float_as_uint(ftc.x + kMagic) - kMagicBits);
+  const int kt1 = (int)(__float_as_uint(ftc.y + kMagic) - kMagicBits);
+  const int kp0 = (int)(__float_as_uint(fpc.x + kMagic) - kMagicBits);
+  const int kp1 = (int)(__float_as_uint(fpc.y + kMagic) - kMagicBits);
+  int nt0 = kt0 + (frt.x >= 0.5f ? 1 : 0), nt1 = kt1 + (frt.y >= 0.5f ? 1 : 0);
+  int np0 = kp0 + (frp.x >= 0.5f ? 1 : 0), np1 = kp1 + (frp.y >= 0.5f ? 1 : 0);
   // pending exact decisions (bit 0/1: element 0 theta/phi, bit 2/3: element 1)
   uint32_t pend = 0;
   if (!gen0) {
-    pend |= (fabsf(e.fr_t.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(e.fr_p.x - 0.5f) <= kEps ? 2u : 0u);
+    pend |= (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
   }
   if (!gen1) {
-    pend |= (fabsf(e.fr_t.y - 0.5f) <= kEps ? 4u : 0u) | (fabsf(e.fr_p.y - 0.5f) <= kEps ? 8u : 0u);
+    pend |= (fabsf(frt.y - 0.5f) <= kEps ? 4u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 8u : 0u);
   }
   while (__any_sync(0xffffffffu, pend != 0u)) {
     if (pend) {
@@ -427,8 +489,9 @@ __device__ __forceinline__ void encode2(float2 x, float2 y, float2 z, const DevF
   const uint32_t lo1 = ((uint32_t)np1 << 18) | (uint32_t)nt1;
   w0 = ((uint64_t)hi0 << 32) | lo0;
   w1 = ((uint64_t)hi1 << 32) | lo1;
-  if (gen0) w0 = encode_generic(x.x, y.x, z.x, F, tab_t, tab_p);
-  if (gen1) w1 = encode_generic(x.y, y.y, z.y, F, tab_t, tab_p);
+  fl0 = fl1 = 0u;
+  if (gen0) w0 = encode_generic(x.x, y.x, z.x, F, tab_t, tab_p, fl0);
+  if (gen1) w1 = encode_generic(x.y, y.y, z.y, F, tab_t, tab_p, fl1);
 }
 
 // Decodes two words through the fast path, falling back per element.

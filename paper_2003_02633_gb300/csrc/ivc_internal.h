@@ -24,6 +24,8 @@ enum KernelKind : int {
   K_UPDATE_FAST = 9,
   K_BATCH_ADD_FAST = 10,
   K_BATCH_AXPY_FAST = 11,
+  K_COMPRESS_FAST = 12,
+  K_DECOMPRESS_FAST = 13,
 };
 
 struct LaunchShape {
@@ -75,6 +77,10 @@ cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_
                             int64_t n, const LaunchShape &s, cudaStream_t st);
 cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
                              int64_t n, const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_compress_fast(const DevFormat &F, const float *xyz, int64_t n, uint64_t *w,
+                                 ivc_counts *counts, const LaunchShape &s, cudaStream_t st);
+cudaError_t launch_decompress_fast(const DevFormat &F, const uint64_t *w, int64_t n, float *xyz,
+                                   const LaunchShape &s, cudaStream_t st);
 cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, const uint64_t *f,
                                const float *rho, uint64_t *v_out, uint64_t *m_out, int64_t n,
                                const LaunchShape &s, cudaStream_t st);

@@ -16,13 +16,24 @@ namespace ivc {
   const TabEntry *tab_t = ivc_smem_tab;                           \
   const TabEntry *tab_p = ivc_smem_tab + (MAP == MAP_TANH ? 0 : F.nent_t)
 
-__device__ __forceinline__ void flush_counts(uint32_t flags, ivc_counts *counts) {
+// Per-thread range-event counters (overflow, underflow, NaN).
+struct Events {
+  uint32_t o = 0, u = 0, q = 0;
+  __device__ __forceinline__ void add(uint32_t flags) {
+    o += flags & 1u;
+    u += (flags >> 1) & 1u;
+    q += (flags >> 2) & 1u;
+  }
+};
+
+// Sums the counters over the warp and adds them to the device counts.
+__device__ __forceinline__ void flush_counts(const Events &ev, ivc_counts *counts) {
   if (counts == nullptr) return;
   const unsigned m = __activemask();
   const int lead = __ffs(m) - 1;
-  const unsigned o = __popc(__ballot_sync(m, flags & 1u));
-  const unsigned u = __popc(__ballot_sync(m, flags & 2u));
-  const unsigned q = __popc(__ballot_sync(m, flags & 4u));
+  const unsigned o = __reduce_add_sync(m, ev.o);
+  const unsigned u = __reduce_add_sync(m, ev.u);
+  const unsigned q = __reduce_add_sync(m, ev.q);
   if ((int)(threadIdx.x & 31) == lead) {
     if (o) atomicAdd(&counts->n_overflow, (unsigned long long)o);
     if (u) atomicAdd(&counts->n_underflow, (unsigned long long)u);
@@ -38,9 +49,10 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ DevFor
                                                   int64_t ld, int64_t n, uint64_t *w,
                                                   ivc_counts *counts) {
   IVC_TABLES(F, MAP);
-  uint32_t flags = 0;
+  Events ev;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t flags = 0;
     float x, y, z;
     if (layout == IVC_AOS) {
       x = __ldcs(xyz + 3 * i);
@@ -53,8 +65,9 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ DevFor
     }
     __stcs(reinterpret_cast<unsigned long long *>(w) + i,
            (unsigned long long)encode_vec<MAP>(x, y, z, F, tab_t, tab_p, flags));
+    ev.add(flags);
   }
-  flush_counts(flags, counts);
+  flush_counts(ev, counts);
 }
 
 // ---------------------------------------------------------------- decompress
@@ -223,7 +236,8 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
       sz = fast::fma2(fast::bc(alpha), uz, vz);
     }
     uint64_t w0, w1;
-    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1);
+    uint32_t f0, f1;
+    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1, f0, f1);
     if (act) __stcs(c2 + i, make_ulonglong2(w0, w1));
   }
   if ((n & 1) && warp == 0 && lane == 0) {
@@ -244,6 +258,75 @@ __global__ void __launch_bounds__(256) k_fused_fast(const __grid_constant__ DevF
   fused_fast_range<OP>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                        ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t,
                        tab_p);
+}
+
+// Compress n AoS vectors (primary layout), two per thread; counts as in
+// k_compress.  Requires a 8-byte aligned xyz and a 16-byte aligned w.
+__global__ void __launch_bounds__(256) k_compress_fast(const __grid_constant__ DevFormat F,
+                                                       const float *__restrict__ xyz, int64_t n,
+                                                       uint64_t *w, ivc_counts *counts) {
+  IVC_TABLES(F, MAP_UNIFORM);
+  const int64_t n2 = n >> 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float2 *v2 = reinterpret_cast<const float2 *>(xyz);
+  ulonglong2 *w2 = reinterpret_cast<ulonglong2 *>(w);
+  Events ev;
+  for (int64_t base = warp * 32; base < n2; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    const bool act = i < n2;
+    // floats 6i .. 6i+5: x0 y0 z0 x1 y1 z1
+    float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0;
+    if (act) {
+      p0 = __ldcs(v2 + 3 * i);
+      p1 = __ldcs(v2 + 3 * i + 1);
+      p2 = __ldcs(v2 + 3 * i + 2);
+    }
+    uint64_t w0, w1;
+    uint32_t f0, f1;
+    fast::encode2(make_float2(p0.x, p1.y), make_float2(p0.y, p2.x), make_float2(p1.x, p2.y), F,
+                  tab_t, tab_p, w0, w1, f0, f1);
+    if (act) {
+      __stcs(w2 + i, make_ulonglong2(w0, w1));
+      ev.add(f0);
+      ev.add(f1);
+    }
+  }
+  if ((n & 1) && warp == 0 && lane == 0) {
+    const int64_t i = n - 1;
+    uint32_t f = 0;
+    w[i] = encode_vec<MAP_UNIFORM>(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], F, tab_t, tab_p, f);
+    ev.add(f);
+  }
+  flush_counts(ev, counts);
+}
+
+// Decompress n words (primary layout) to AoS FP32, two per thread.  Requires
+// a 16-byte aligned w and an 8-byte aligned xyz.
+__global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__ DevFormat F,
+                                                         const uint64_t *__restrict__ w,
+                                                         int64_t n, float *xyz) {
+  IVC_TABLES(F, MAP_UNIFORM);
+  const int64_t n2 = n >> 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(w);
+  float2 *v2 = reinterpret_cast<float2 *>(xyz);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const ulonglong2 ww = __ldcs(w2 + i);
+    float2 X, Y, Z;
+    fast::decode2_full(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z);
+    __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
+    __stcs(v2 + 3 * i + 1, make_float2(Z.x, X.y));
+    __stcs(v2 + 3 * i + 2, make_float2(Y.y, Z.y));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
+    const float3 v = decode_word<MAP_UNIFORM>(w[i], F, tab_t, tab_p);
+    xyz[3 * i] = v.x;
+    xyz[3 * i + 1] = v.y;
+    xyz[3 * i + 2] = v.z;
+  }
 }
 
 // v_out = encode(fmaf(dt, f, v)); m_out = encode(rho * v_new) (if requested).
@@ -273,13 +356,14 @@ __global__ void __launch_bounds__(256) k_update_fast(const __grid_constant__ Dev
     const float2 sy = fast::fma2(fast::bc(dt), gy, uy);
     const float2 sz = fast::fma2(fast::bc(dt), gz, uz);
     uint64_t w0, w1;
-    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1);
+    uint32_t f0, f1;
+    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1, f0, f1);
     if (act) __stcs(o2 + i, make_ulonglong2(w0, w1));
     if (want_m) {
       const float2 q = act ? make_float2(__ldcs(rho + 2 * i), __ldcs(rho + 2 * i + 1))
                            : make_float2(0.0f, 0.0f);
       fast::encode2(fast::mul2(q, sx), fast::mul2(q, sy), fast::mul2(q, sz), F, tab_t, tab_p, w0,
-                    w1);
+                    w1, f0, f1);
       if (act) __stcs(m2 + i, make_ulonglong2(w0, w1));
     }
   }
@@ -479,6 +563,18 @@ cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x,
   return cudaGetLastError();
 }
 
+cudaError_t launch_compress_fast(const DevFormat &F, const float *xyz, int64_t n, uint64_t *w,
+                                 ivc_counts *counts, const LaunchShape &s, cudaStream_t st) {
+  k_compress_fast<<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decompress_fast(const DevFormat &F, const uint64_t *w, int64_t n, float *xyz,
+                                   const LaunchShape &s, cudaStream_t st) {
+  k_decompress_fast<<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, const uint64_t *f,
                                const float *rho, uint64_t *v_out, uint64_t *m_out, int64_t n,
                                const LaunchShape &s, cudaStream_t st) {
@@ -505,6 +601,8 @@ static const void *kernel_ptr(int kind) {
     case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY>;
     case K_UPDATE_FAST: return (const void *)k_update_fast;
     case K_BATCH_ADD_FAST: return (const void *)k_batched_fast<IVC_OP_ADD>;
+    case K_COMPRESS_FAST: return (const void *)k_compress_fast;
+    case K_DECOMPRESS_FAST: return (const void *)k_decompress_fast;
     case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY>;
     default: return (const void *)k_batched<MAP, IVC_OP_AXPY>;
   }

@@ -1,7 +1,7 @@
 """Host checks of the constants the fast path's bin-coordinate estimate relies
-on (no GPU): the atan polynomial in ivc_fast.cuh, evaluated in FP32 Horner
-form exactly as the kernel does, stays within the error budget that the
-0.03-bin ambiguity band assumes."""
+on (no GPU): atan_ratio2 in ivc_fast.cuh, emulated in FP32 with the kernel's
+operation order, stays within the error budget that the ambiguity band kEps
+assumes (exact side tests run for every fraction within kEps of 1/2)."""
 import os
 import re
 
@@ -9,35 +9,80 @@ import numpy as np
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_2003_02633_gb300", "csrc", "ivc_fast.cuh")
+F32 = np.float32
 
 
-def _atan_coeffs():
+def _body(name, end):
     src = open(SRC).read()
-    body = src[src.index("float2 atan01("):]
-    body = body[:body.index("return mul2(p, q);")]
-    return [float(x) for x in re.findall(r"bc\((-?[0-9.e-]+)f\)", body)]
+    body = src[src.index(name):]
+    return body[:body.index(end)]
 
 
-def test_atan_polynomial_error_budget():
-    c = np.array(_atan_coeffs(), dtype=np.float32)
-    assert len(c) == 8
-    q = np.linspace(0.0, 1.0, 400001).astype(np.float32)
-    q2 = (q * q).astype(np.float32)
-    p = np.full_like(q, c[0])
+def _r_coeffs():
+    body = _body("void atan_ratio2(", "const float2 sv")
+    return [float(x) for x in re.findall(r"bc\((-?[0-9.e-]+)f\)", body)
+            if x not in ("1.0", "-0.5")]
+
+
+def _fma(a, b, c):
+    # FP32 products are exact in FP64; the sum is rounded (FP64 then FP32)
+    return (a.astype(np.float64) * b + c).astype(F32)
+
+
+def _atan_ratio(mn, mx):
+    """The kernel's steps: Newton-refined reciprocal, double-float quotient,
+    q + q^3 R(q^2) with the ql term at slope 1 - q^2/2."""
+    m = np.maximum(mx, F32(1e-30))
+    r = (F32(1.0) / m).astype(F32)
+    r = _fma(r, _fma(-m, r, np.ones_like(m)), r)
+    qh = (mn * r).astype(F32)
+    ql = (_fma(-m, qh, mn) * r).astype(F32)
+    q2 = (qh * qh).astype(F32)
+    c = _r_coeffs()
+    R = np.full_like(q2, F32(c[0]))
     for k in c[1:]:
-        p = (p * q2 + k).astype(np.float32)
-    r = (p * q).astype(np.float32).astype(np.float64)
-    err = np.abs(r - np.arctan(q.astype(np.float64))).max()
-    # 2e-7 rad is below 0.01 bin for both angle grids of <0,7,22>-17-18
-    assert err < 2e-7
-    bins_theta = err * ((1 << 18) - 1) / (2 * np.pi)
-    bins_phi = err * ((1 << 17) - 1) / np.pi
-    assert max(bins_theta, bins_phi) < 0.01
+        R = _fma(R, q2, np.full_like(q2, F32(k)))
+    sv = ((qh * q2).astype(F32) * R).astype(F32)
+    bl = _fma(ql, _fma(q2, np.full_like(q2, F32(-0.5)), np.ones_like(q2)), sv)
+    return qh, bl
+
+
+def _max_err_rad():
+    rng = np.random.default_rng(7)
+    mx = rng.uniform(0.5, 4.0, 400000).astype(F32)
+    mn = (mx * rng.uniform(0.0, 1.0, mx.size)).astype(F32)
+    mn = np.minimum(mn, mx)
+    # the whole ratio range, with q = 1 and q -> 0 included
+    mn[:4] = [mx[0], 0.0, mx[2] * F32(1e-6), mx[3] * F32(0.999999)]
+    bh, bl = _atan_ratio(mn, mx)
+    exact = np.arctan(mn.astype(np.float64) / mx.astype(np.float64))
+    return float(np.abs(bh.astype(np.float64) + bl - exact).max())
+
+
+def test_r_coefficients_present():
+    c = _r_coeffs()
+    assert len(c) == 8
+    # leading term of atan(q) = q - q^3/3 + ...: R(0) = -1/3
+    assert abs(c[-1] + 1.0 / 3.0) < 1e-4
+
+
+def test_atan_ratio_error():
+    assert _max_err_rad() < 5e-8
 
 
 def test_estimate_flag_band_covers_budget():
     src = open(SRC).read()
     eps = float(re.search(r"kEps = ([0-9.]+)f", src).group(1))
-    # polynomial (0.006) + quotient after one Newton step (< 0.0001) + FP32
-    # rounding of g, N/4 - g, N/2 - u (0.002 + 0.002 + 0.004) bins
-    assert eps >= 0.006 + 0.0001 + 0.008
+    err = _max_err_rad()
+    n_theta, n_phi = (1 << 18) - 1, (1 << 17) - 1
+    poly = err * max(n_theta / (2 * np.pi), n_phi / np.pi)
+    # rho = sqrt(x^2 + y^2) after one Newton step on the double-float sum:
+    # the final FMA's rounding, half an ulp, relative error <= 2^-24 (the
+    # Newton residual is quadratic in rsqrt's 2^-22 and negligible);
+    # d beta = (rho |z| / (rho^2 + z^2)) d rho / rho <= d rho / (2 rho)
+    rho = 2.0 ** -24 / 2 * n_phi / np.pi
+    # bin_coord2: C (double-float) times beta rounded once in the tail terms
+    tail = 2e-4
+    budget = poly + rho + tail
+    assert budget < 0.0045
+    assert eps >= budget + 0.0005
