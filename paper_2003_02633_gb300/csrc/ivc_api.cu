@@ -290,7 +290,7 @@ LaunchShape ivc::default_shape(int map, int kind, const DevFormat &F, int64_t n,
   s.block = (cfg && cfg->block > 0) ? cfg->block : 256;
   if (s.block > 256) s.block = 256;
   s.vec2 = vec2;
-  s.smem = table_smem_bytes(F, map);
+  s.smem = kernel_smem_bytes(F, map, kind, s.block);
   int bps = (cfg && cfg->blocks_per_sm > 0) ? cfg->blocks_per_sm : 0;
   const int occ = occupancy(map, kind, s.block, s.smem);
   if (bps <= 0 || (occ > 0 && bps > occ)) bps = occ > 0 ? occ : 1;
@@ -560,7 +560,7 @@ ivc_status ivc_plan_batched(const ivc_format *fmt, ivc_op op, const ivc_field *f
   LaunchShape s;
   s.block = (cfg && cfg->block > 0 && cfg->block <= 256) ? cfg->block : 256;
   s.vec2 = 1;
-  s.smem = table_smem_bytes(p->F, p->map);
+  s.smem = kernel_smem_bytes(p->F, p->map, kind, s.block);
   const int occ = occupancy(p->map, kind, s.block, s.smem);
   int bps = (cfg && cfg->blocks_per_sm > 0) ? cfg->blocks_per_sm : occ;
   if (occ > 0 && bps > occ) bps = occ;
@@ -644,9 +644,9 @@ ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const u
   ivc_launch_config bc{256, vec2 ? 2 : 1, 8192, 0};
   const bool fast_kind = vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F);
   for (int blk : blocks) {
-    const size_t smem = table_smem_bytes(F, map);
-    const int occ = occupancy(map, fast_kind ? (op == IVC_OP_ADD ? K_ADD_FAST : K_AXPY_FAST) : kind,
-                              blk, smem);
+    const int okind = fast_kind ? (op == IVC_OP_ADD ? K_ADD_FAST : K_AXPY_FAST) : kind;
+    const size_t smem = kernel_smem_bytes(F, map, okind, blk);
+    const int occ = occupancy(map, okind, blk, smem);
     for (int bps = 1; bps <= occ; bps *= 2) {
       ivc_launch_config cfg{blk, vec2 ? 2 : 1, 8192, bps};
       LaunchShape s = default_shape(map, kind, F, n, vec2, &cfg);

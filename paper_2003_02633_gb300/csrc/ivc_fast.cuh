@@ -397,13 +397,27 @@ static __device__ __noinline__ float3 decode_generic(uint64_t w, const DevFormat
   return decode_word<MAP_UNIFORM>(w, F, tab_t, tab_p);
 }
 
-// Encodes two vectors.  All lanes of the warp must call it (warp loop).
-// fl0 / fl1 receive the range events of each vector (bit 0 overflow, 1
-// underflow, 2 NaN); only vectors on the generic path can raise them.
-__device__ __forceinline__ void encode2(float2 x, float2 y, float2 z, const DevFormat &F,
+__device__ __forceinline__ uint64_t pack_word(uint32_t hi, int np, int nt) {
+  return ((uint64_t)(hi | ((uint32_t)np >> 14)) << 32) | (((uint32_t)np << 18) | (uint32_t)nt);
+}
+
+// Result of encode2 for two vectors: provisional words and what the deferred
+// exact tests need.
+struct Enc2 {
+  uint64_t w0, w1;         // words (provisional where pend != 0)
+  uint32_t fl0, fl1;       // range events (bit 0 overflow, 1 underflow, 2 NaN)
+  uint32_t pend0, pend1;   // pending kinds: bit 0 theta, bit 1 phi
+  int nt0, nt1, np0, np1;  // k of a pending kind, else the code
+  uint32_t hi0, hi1;       // high words without the n_phi bits
+};
+
+// Encodes two vectors.  The word of a vector with a pending exact decision
+// is provisional: the caller queues it with push2.  Range events (fl0 / fl1)
+// come only from vectors on the generic path.
+__device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevFormat &F,
                                         const TabEntry *__restrict__ tab_t,
-                                        const TabEntry *__restrict__ tab_p, uint64_t &w0,
-                                        uint64_t &w1, uint32_t &fl0, uint32_t &fl1) {
+                                        const TabEntry *__restrict__ tab_p) {
+  Enc2 r;
   // |x|_inf in [2^-32, 2^32): no scaling, no range limits, no specials
   // (integer max of the magnitude bits: NaN compares above every finite value)
   const uint32_t am0 = max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(y.x) & 0x7fffffffu),
@@ -456,42 +470,112 @@ __device__ __forceinline__ void encode2(float2 x, float2 y, float2 z, const DevF
   const int kp1 = (int)(__float_as_uint(fpc.y + kMagic) - kMagicBits);
   int nt0 = kt0 + (frt.x >= 0.5f ? 1 : 0), nt1 = kt1 + (frt.y >= 0.5f ? 1 : 0);
   int np0 = kp0 + (frp.x >= 0.5f ? 1 : 0), np1 = kp1 + (frp.y >= 0.5f ? 1 : 0);
-  // pending exact decisions (bit 0/1: element 0 theta/phi, bit 2/3: element 1)
-  uint32_t pend = 0;
-  if (!gen0) {
-    pend |= (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
-  }
-  if (!gen1) {
-    pend |= (fabsf(frt.y - 0.5f) <= kEps ? 4u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 8u : 0u);
-  }
-  while (__any_sync(0xffffffffu, pend != 0u)) {
-    if (pend) {
-      const int j = __ffs(pend) - 1;
-      pend &= pend - 1u;
-      const bool el = j >= 2;
-      const int kind = j & 1;
-      const int k = kind ? (el ? kp1 : kp0) : (el ? kt1 : kt0);
-      const int side = exact_side(kind, k, el ? x.y : x.x, el ? y.y : y.x, el ? z.y : z.x, F,
-                                  tab_t, tab_p);
-      if (j == 0) nt0 = kt0 + side;
-      else if (j == 1) np0 = kp0 + side;
-      else if (j == 2) nt1 = kt1 + side;
-      else np1 = kp1 + side;
-    }
-  }
+  // pending exact decisions: kinds within kEps of a rounding boundary
+  // (bit 0 theta, bit 1 phi); their words are provisional
+  r.pend0 = gen0 ? 0u : (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
+  r.pend1 = gen1 ? 0u : (fabsf(frt.y - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 2u : 0u);
+  r.nt0 = (r.pend0 & 1u) ? kt0 : nt0;
+  r.nt1 = (r.pend1 & 1u) ? kt1 : nt1;
+  r.np0 = (r.pend0 & 2u) ? kp0 : np0;
+  r.np1 = (r.pend1 & 2u) ? kp1 : np1;
   // canonical forms and packing (Fig. manbit)
   if (nt0 == kN || np0 == 0 || np0 == kM) nt0 = 0;
   if (nt1 == kN || np1 == 0 || np1 == kM) nt1 = 0;
   const uint32_t rb0 = __float_as_uint(r32.x), rb1 = __float_as_uint(r32.y);
-  const uint32_t hi0 = (((rb0 - (47u << 23)) << 2) & 0xFFFFFFF8u) | ((uint32_t)np0 >> 14);
-  const uint32_t hi1 = (((rb1 - (47u << 23)) << 2) & 0xFFFFFFF8u) | ((uint32_t)np1 >> 14);
-  const uint32_t lo0 = ((uint32_t)np0 << 18) | (uint32_t)nt0;
-  const uint32_t lo1 = ((uint32_t)np1 << 18) | (uint32_t)nt1;
-  w0 = ((uint64_t)hi0 << 32) | lo0;
-  w1 = ((uint64_t)hi1 << 32) | lo1;
-  fl0 = fl1 = 0u;
-  if (gen0) w0 = encode_generic(x.x, y.x, z.x, F, tab_t, tab_p, fl0);
-  if (gen1) w1 = encode_generic(x.y, y.y, z.y, F, tab_t, tab_p, fl1);
+  r.hi0 = ((rb0 - (47u << 23)) << 2) & 0xFFFFFFF8u;
+  r.hi1 = ((rb1 - (47u << 23)) << 2) & 0xFFFFFFF8u;
+  r.w0 = pack_word(r.hi0, np0, nt0);
+  r.w1 = pack_word(r.hi1, np1, nt1);
+  r.fl0 = r.fl1 = 0u;
+  if (gen0) r.w0 = encode_generic(x.x, y.x, z.x, F, tab_t, tab_p, r.fl0);
+  if (gen1) r.w1 = encode_generic(x.y, y.y, z.y, F, tab_t, tab_p, r.fl1);
+  return r;
+}
+
+// ---------------------------------------------------- deferred exact tests
+// A vector whose bin coordinate lies within kEps of a rounding boundary gets
+// a provisional word; its exact side-of-boundary tests run later from a
+// per-warp queue in shared memory, one item per lane, 32 at a time, and the
+// final word overwrites the provisional one (same warp, ordered by
+// __syncwarp).  Capacity: at most 31 items wait between pushes and one push
+// adds at most 64.
+constexpr int kQueueCap = 96;
+
+struct PendItem {
+  uint64_t *dst;   // word to overwrite
+  float x, y, z;   // the encoded vector
+  uint32_t hi;     // high word without the n_phi bits
+  int nt;          // theta: k when pending, else the code
+  uint32_t npp;    // phi: k when pending, else the code (bits 0..16); kinds (bits 30..31)
+};
+
+struct WarpQueue {
+  PendItem *q;     // this warp's slots
+  int count;       // warp-uniform
+};
+
+__device__ __forceinline__ WarpQueue warp_queue(void *base) {
+  WarpQueue wq;
+  wq.q = reinterpret_cast<PendItem *>(base) + (threadIdx.x >> 5) * kQueueCap;
+  wq.count = 0;
+  return wq;
+}
+
+// Runs once per 32 queued items: kept out of line so that the main loop's
+// register allocation does not carry the exact test.
+static __device__ __noinline__ void resolve_item(const PendItem *pit, const DevFormat &F,
+                                                 const TabEntry *tab_t, const TabEntry *tab_p) {
+  const PendItem it = *pit;
+  int nt = it.nt;
+  int np = (int)(it.npp & 0x1FFFFu);
+  const uint32_t pend = it.npp >> 30;
+  // one kind-agnostic test per item; a second only when both kinds wait
+  const int kind = (pend & 1u) ? 0 : 1;
+  const int side = exact_side(kind, kind ? np : nt, it.x, it.y, it.z, F, tab_t, tab_p);
+  if (kind == 0) nt += side;
+  else np += side;
+  if (pend == 3u) np += exact_side(1, np, it.x, it.y, it.z, F, tab_t, tab_p);
+  if (nt == kN || np == 0 || np == kM) nt = 0;
+  *it.dst = pack_word(it.hi, np, nt);
+}
+
+// Queues the pending vectors of one encode2 result (element 0 -> dst0,
+// element 1 -> dst0 + 1; inactive lanes queue nothing) and resolves full
+// batches.  All lanes of the warp call it.
+__device__ __forceinline__ void push2(WarpQueue &wq, bool act, const Enc2 &e, float2 x, float2 y,
+                                      float2 z, uint64_t *dst0, const DevFormat &F,
+                                      const TabEntry *tab_t, const TabEntry *tab_p) {
+  const uint32_t p0 = act ? e.pend0 : 0u, p1 = act ? e.pend1 : 0u;
+  const unsigned b0 = __ballot_sync(0xffffffffu, p0 != 0u);
+  const unsigned b1 = __ballot_sync(0xffffffffu, p1 != 0u);
+  if ((b0 | b1) == 0u) return;
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+  int slot = wq.count + __popc(b0 & lt) + __popc(b1 & lt);
+  if (p0) {
+    wq.q[slot++] = PendItem{dst0, x.x, y.x, z.x, e.hi0, e.nt0, (uint32_t)e.np0 | (p0 << 30)};
+  }
+  if (p1) {
+    wq.q[slot] = PendItem{dst0 + 1, x.y, y.y, z.y, e.hi1, e.nt1, (uint32_t)e.np1 | (p1 << 30)};
+  }
+  wq.count += __popc(b0) + __popc(b1);
+  while (wq.count >= 32) {
+    __syncwarp();
+    resolve_item(wq.q + wq.count - 32 + (threadIdx.x & 31), F, tab_t, tab_p);
+    wq.count -= 32;
+    __syncwarp();
+  }
+}
+
+// Resolves what is left in the queue (all lanes call it).
+__device__ __forceinline__ void drain(WarpQueue &wq, const DevFormat &F, const TabEntry *tab_t,
+                                      const TabEntry *tab_p) {
+  if (wq.count == 0) return;
+  __syncwarp();
+  if ((int)(threadIdx.x & 31) < wq.count) {
+    resolve_item(wq.q + (threadIdx.x & 31), F, tab_t, tab_p);
+  }
+  wq.count = 0;
+  __syncwarp();
 }
 
 // Decodes two words through the fast path, falling back per element.

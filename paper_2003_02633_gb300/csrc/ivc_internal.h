@@ -57,6 +57,9 @@ struct PlanDev {
 };
 
 size_t table_smem_bytes(const DevFormat &F, int map);
+// Dynamic shared memory of a kernel kind: tables, plus the per-warp queues of
+// deferred exact tests for the fast kernels that encode.
+size_t kernel_smem_bytes(const DevFormat &F, int map, int kind, int block);
 
 cudaError_t launch_compress(int map, const DevFormat &F, const float *xyz, int layout, int64_t ld,
                             int64_t n, uint64_t *w, ivc_counts *counts, const LaunchShape &s,

@@ -16,6 +16,9 @@ namespace ivc {
   const TabEntry *tab_t = ivc_smem_tab;                           \
   const TabEntry *tab_p = ivc_smem_tab + (MAP == MAP_TANH ? 0 : F.nent_t)
 
+// Deferred-test queues of the fast kernels: shared memory after the tables.
+#define IVC_QUEUE(F) ((void *)(ivc_smem_tab + (F).nent_t + (F).nent_p))
+
 // Per-thread range-event counters (overflow, underflow, NaN).
 struct Events {
   uint32_t o = 0, u = 0, q = 0;
@@ -214,16 +217,27 @@ template <int OP>
 __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64_t *b, uint64_t *c,
                                                  int64_t n, int64_t warp, int64_t nwarps, int lane,
                                                  float alpha, const DevFormat &F,
-                                                 const TabEntry *tab_t, const TabEntry *tab_p) {
+                                                 const TabEntry *tab_t, const TabEntry *tab_p,
+                                                 void *qbase) {
+  fast::WarpQueue wq = fast::warp_queue(qbase);
   const int64_t n2 = n >> 1;
   const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(a);
   const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(b);
   ulonglong2 *c2 = reinterpret_cast<ulonglong2 *>(c);
+  // the next iteration's words are loaded before this iteration's arithmetic
+  ulonglong2 na = make_ulonglong2(0ull, 0ull), nb = na;
+  if (warp * 32 + lane < n2) {
+    na = __ldcs(a2 + warp * 32 + lane);
+    nb = __ldcs(b2 + warp * 32 + lane);
+  }
   for (int64_t base = warp * 32; base < n2; base += nwarps * 32) {
     const int64_t i = base + lane;
     const bool act = i < n2;
-    const ulonglong2 wa = act ? __ldcs(a2 + i) : make_ulonglong2(0ull, 0ull);
-    const ulonglong2 wb = act ? __ldcs(b2 + i) : make_ulonglong2(0ull, 0ull);
+    const ulonglong2 wa = na, wb = nb;
+    if (i + nwarps * 32 < n2) {
+      na = __ldcs(a2 + i + nwarps * 32);
+      nb = __ldcs(b2 + i + nwarps * 32);
+    }
     float2 ux, uy, uz, vx, vy, vz;
     fast::decode2_full(wa.x, wa.y, F, tab_t, tab_p, ux, uy, uz);
     fast::decode2_full(wb.x, wb.y, F, tab_t, tab_p, vx, vy, vz);
@@ -235,11 +249,11 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
       sy = fast::fma2(fast::bc(alpha), uy, vy);
       sz = fast::fma2(fast::bc(alpha), uz, vz);
     }
-    uint64_t w0, w1;
-    uint32_t f0, f1;
-    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1, f0, f1);
-    if (act) __stcs(c2 + i, make_ulonglong2(w0, w1));
+    const fast::Enc2 e = fast::encode2(sx, sy, sz, F, tab_t, tab_p);
+    if (act) __stcs(c2 + i, make_ulonglong2(e.w0, e.w1));
+    fast::push2(wq, act, e, sx, sy, sz, c + 2 * i, F, tab_t, tab_p);
   }
+  fast::drain(wq, F, tab_t, tab_p);
   if ((n & 1) && warp == 0 && lane == 0) {
     uint32_t flags = 0;
     const int64_t i = n - 1;
@@ -257,12 +271,12 @@ __global__ void __launch_bounds__(256) k_fused_fast(const __grid_constant__ DevF
   IVC_TABLES(F, MAP_UNIFORM);
   fused_fast_range<OP>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                        ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t,
-                       tab_p);
+                       tab_p, IVC_QUEUE(F));
 }
 
 // Compress n AoS vectors (primary layout), two per thread; counts as in
 // k_compress.  Requires a 8-byte aligned xyz and a 16-byte aligned w.
-__global__ void __launch_bounds__(256) k_compress_fast(const __grid_constant__ DevFormat F,
+__global__ void __launch_bounds__(256, 3) k_compress_fast(const __grid_constant__ DevFormat F,
                                                        const float *__restrict__ xyz, int64_t n,
                                                        uint64_t *w, ivc_counts *counts) {
   IVC_TABLES(F, MAP_UNIFORM);
@@ -272,27 +286,36 @@ __global__ void __launch_bounds__(256) k_compress_fast(const __grid_constant__ D
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float2 *v2 = reinterpret_cast<const float2 *>(xyz);
   ulonglong2 *w2 = reinterpret_cast<ulonglong2 *>(w);
+  fast::WarpQueue wq = fast::warp_queue(IVC_QUEUE(F));
   Events ev;
+  // floats 6i .. 6i+5: x0 y0 z0 x1 y1 z1; the next iteration's are loaded
+  // before this iteration's arithmetic
+  float2 q0 = make_float2(0.0f, 0.0f), q1 = q0, q2 = q0;
+  if (warp * 32 + lane < n2) {
+    q0 = __ldcs(v2 + 3 * (warp * 32 + lane));
+    q1 = __ldcs(v2 + 3 * (warp * 32 + lane) + 1);
+    q2 = __ldcs(v2 + 3 * (warp * 32 + lane) + 2);
+  }
   for (int64_t base = warp * 32; base < n2; base += nwarps * 32) {
     const int64_t i = base + lane;
     const bool act = i < n2;
-    // floats 6i .. 6i+5: x0 y0 z0 x1 y1 z1
-    float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0;
-    if (act) {
-      p0 = __ldcs(v2 + 3 * i);
-      p1 = __ldcs(v2 + 3 * i + 1);
-      p2 = __ldcs(v2 + 3 * i + 2);
+    const float2 p0 = q0, p1 = q1, p2 = q2;
+    if (i + nwarps * 32 < n2) {
+      q0 = __ldcs(v2 + 3 * (i + nwarps * 32));
+      q1 = __ldcs(v2 + 3 * (i + nwarps * 32) + 1);
+      q2 = __ldcs(v2 + 3 * (i + nwarps * 32) + 2);
     }
-    uint64_t w0, w1;
-    uint32_t f0, f1;
-    fast::encode2(make_float2(p0.x, p1.y), make_float2(p0.y, p2.x), make_float2(p1.x, p2.y), F,
-                  tab_t, tab_p, w0, w1, f0, f1);
+    const float2 vx = make_float2(p0.x, p1.y), vy = make_float2(p0.y, p2.x),
+                 vz = make_float2(p1.x, p2.y);
+    const fast::Enc2 e = fast::encode2(vx, vy, vz, F, tab_t, tab_p);
     if (act) {
-      __stcs(w2 + i, make_ulonglong2(w0, w1));
-      ev.add(f0);
-      ev.add(f1);
+      __stcs(w2 + i, make_ulonglong2(e.w0, e.w1));
+      ev.add(e.fl0);
+      ev.add(e.fl1);
     }
+    fast::push2(wq, act, e, vx, vy, vz, w + 2 * i, F, tab_t, tab_p);
   }
+  fast::drain(wq, F, tab_t, tab_p);
   if ((n & 1) && warp == 0 && lane == 0) {
     const int64_t i = n - 1;
     uint32_t f = 0;
@@ -312,8 +335,11 @@ __global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(w);
   float2 *v2 = reinterpret_cast<float2 *>(xyz);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-    const ulonglong2 ww = __ldcs(w2 + i);
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  ulonglong2 nw = i0 < n2 ? __ldcs(w2 + i0) : make_ulonglong2(0ull, 0ull);  // next words
+  for (int64_t i = i0; i < n2; i += stride) {
+    const ulonglong2 ww = nw;
+    if (i + stride < n2) nw = __ldcs(w2 + i + stride);
     float2 X, Y, Z;
     fast::decode2_full(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z);
     __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
@@ -330,7 +356,7 @@ __global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__
 }
 
 // v_out = encode(fmaf(dt, f, v)); m_out = encode(rho * v_new) (if requested).
-__global__ void __launch_bounds__(256) k_update_fast(const __grid_constant__ DevFormat F, float dt,
+__global__ void __launch_bounds__(256, 3) k_update_fast(const __grid_constant__ DevFormat F, float dt,
                                                      const uint64_t *v, const uint64_t *f,
                                                      const float *__restrict__ rho,
                                                      uint64_t *v_out, uint64_t *m_out, int64_t n) {
@@ -344,29 +370,39 @@ __global__ void __launch_bounds__(256) k_update_fast(const __grid_constant__ Dev
   const ulonglong2 *f2 = reinterpret_cast<const ulonglong2 *>(f);
   ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(v_out);
   ulonglong2 *m2 = reinterpret_cast<ulonglong2 *>(m_out);
+  fast::WarpQueue wq = fast::warp_queue(IVC_QUEUE(F));
+  ulonglong2 nv = make_ulonglong2(0ull, 0ull), nf = nv;  // next iteration's words
+  if (warp * 32 + lane < n2) {
+    nv = __ldcs(v2 + warp * 32 + lane);
+    nf = __ldcs(f2 + warp * 32 + lane);
+  }
   for (int64_t base = warp * 32; base < n2; base += nwarps * 32) {
     const int64_t i = base + lane;
     const bool act = i < n2;
-    const ulonglong2 wv = act ? __ldcs(v2 + i) : make_ulonglong2(0ull, 0ull);
-    const ulonglong2 wf = act ? __ldcs(f2 + i) : make_ulonglong2(0ull, 0ull);
+    const ulonglong2 wv = nv, wf = nf;
+    if (i + nwarps * 32 < n2) {
+      nv = __ldcs(v2 + i + nwarps * 32);
+      nf = __ldcs(f2 + i + nwarps * 32);
+    }
     float2 ux, uy, uz, gx, gy, gz;
     fast::decode2_full(wv.x, wv.y, F, tab_t, tab_p, ux, uy, uz);
     fast::decode2_full(wf.x, wf.y, F, tab_t, tab_p, gx, gy, gz);
     const float2 sx = fast::fma2(fast::bc(dt), gx, ux);
     const float2 sy = fast::fma2(fast::bc(dt), gy, uy);
     const float2 sz = fast::fma2(fast::bc(dt), gz, uz);
-    uint64_t w0, w1;
-    uint32_t f0, f1;
-    fast::encode2(sx, sy, sz, F, tab_t, tab_p, w0, w1, f0, f1);
-    if (act) __stcs(o2 + i, make_ulonglong2(w0, w1));
+    const fast::Enc2 e = fast::encode2(sx, sy, sz, F, tab_t, tab_p);
+    if (act) __stcs(o2 + i, make_ulonglong2(e.w0, e.w1));
+    fast::push2(wq, act, e, sx, sy, sz, v_out + 2 * i, F, tab_t, tab_p);
     if (want_m) {
       const float2 q = act ? make_float2(__ldcs(rho + 2 * i), __ldcs(rho + 2 * i + 1))
                            : make_float2(0.0f, 0.0f);
-      fast::encode2(fast::mul2(q, sx), fast::mul2(q, sy), fast::mul2(q, sz), F, tab_t, tab_p, w0,
-                    w1, f0, f1);
-      if (act) __stcs(m2 + i, make_ulonglong2(w0, w1));
+      const float2 mx = fast::mul2(q, sx), my = fast::mul2(q, sy), mz = fast::mul2(q, sz);
+      const fast::Enc2 em = fast::encode2(mx, my, mz, F, tab_t, tab_p);
+      if (act) __stcs(m2 + i, make_ulonglong2(em.w0, em.w1));
+      fast::push2(wq, act, em, mx, my, mz, m_out + 2 * i, F, tab_t, tab_p);
     }
   }
+  fast::drain(wq, F, tab_t, tab_p);
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     uint32_t flags = 0;
     const int64_t i = n - 1;
@@ -459,7 +495,7 @@ __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ De
                         reinterpret_cast<uintptr_t>(c)) & 15u) == 0;
     if (vec2) {
       fused_fast_range<OP>(a, b, c, len, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31,
-                           fd.alpha, F, tab_t, tab_p);
+                           fd.alpha, F, tab_t, tab_p, IVC_QUEUE(F));
     } else if (OP == IVC_OP_ADD) {
       fused_range<MAP_UNIFORM>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAdd{}, F, tab_t,
                                tab_p, flags);
@@ -488,6 +524,14 @@ __global__ void k_tile_scan(const FieldDesc *fields, int nfields, int tile, int6
 
 size_t table_smem_bytes(const DevFormat &F, int map) {
   return map == MAP_TANH ? 0 : (size_t)(F.nent_t + F.nent_p) * sizeof(TabEntry);
+}
+
+size_t kernel_smem_bytes(const DevFormat &F, int map, int kind, int block) {
+  const bool queue = kind == K_ADD_FAST || kind == K_AXPY_FAST || kind == K_UPDATE_FAST ||
+                     kind == K_BATCH_ADD_FAST || kind == K_BATCH_AXPY_FAST ||
+                     kind == K_COMPRESS_FAST;
+  return table_smem_bytes(F, map) +
+         (queue ? (size_t)(block / 32) * fast::kQueueCap * sizeof(fast::PendItem) : 0);
 }
 
 #define IVC_DISPATCH_MAP(map, KERNEL, ...)                                                    \
