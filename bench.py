@@ -46,9 +46,12 @@ def parse_args():
     p.add_argument("--log2n", type=int, default=28)
     p.add_argument("--no-extra", action="store_true", help="skip the baseline/extra measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--workload", choices=["add", "tgv", "batched", "precision"], default="add",
+    p.add_argument("--workload", choices=["add", "tgv", "batched", "precision", "fdiv"],
+                   default="add",
                    help="add: the headline line; the others print their own JSON line")
     p.add_argument("--tgv-elements", type=int, default=96)
+    p.add_argument("--fdiv-elements", type=int, default=96,
+                   help="elements per axis of the flux-divergence mesh")
     return p.parse_args()
 
 
@@ -591,6 +594,74 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fdiv(args):
+    """Algorithm 1 (Sec. 4; Table fr_nse, step 10): divergence of the compressed
+    Euler flux of the TGV initial state on an E^3 hex mesh of degree 3 (64
+    solution points, 5 flux rows per point), against the same operator on the
+    uncompressed FP32 flux; FP32 arithmetic in both."""
+    import numpy as np
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+    dev = torch.device("cuda", 0)
+    fmt = ivc.default_format()
+    E = args.fdiv_elements
+    order, nv = 3, 5
+    ns = (order + 1) ** 3
+    F = synth.tgv_euler_flux(E, order, device=dev)               # (ns, nv, ne, 3)
+    ne = F.shape[2]
+    W = ivc.compress(fmt, F.reshape(-1, 3)).reshape(ns, nv, ne)
+    Fc = F.permute(3, 0, 1, 2).contiguous()                        # (3, ns, nv, ne)
+    del F
+    D = torch.from_numpy(synth.fr_hex_operator(order, 2 * math.pi / E)).to(dev)
+    out = torch.empty((ns, nv, ne), dtype=torch.float32, device=dev)
+    out32 = torch.empty_like(out)
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    steps, warmup = max(3, min(args.steps, 50)), max(3, min(args.warmup, 10))
+    ms, per = time_launches(lambda: ivc.flux_divergence(fmt, W, D, out=out, stream=s), steps,
+                            warmup, stream)
+    ms32, per32 = time_launches(lambda: ivc.f32_flux_divergence(Fc, D, out=out32, stream=s),
+                                steps, warmup, stream)
+    t, t32 = ms / steps, ms32 / steps
+    flop = 2.0 * 3 * ns * ns * nv                                   # per element
+    bytes_c = ns * nv * 8 + ns * nv * 4
+    bytes_32 = ns * nv * 12 + ns * nv * 4
+    hbm_gbs, _ = measured_peaks()
+    # FP32 FMA peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (sm count from the device)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    d = (out.double() - out32.double()).abs()
+    scale = out32.double().abs().max()
+    line = {"workload": "flux_divergence_alg1", "elements": ne, "ns": ns, "nvars": nv,
+            "steps": steps, "ms": round(t, 4), "elements_per_s": round(ne / (t * 1e-3), 1),
+            "gbs_algorithmic": round(bytes_c * ne / (t * 1e-3) / 1e9, 1),
+            "hbm_frac": round(bytes_c * ne / (t * 1e-3) / 1e9 / hbm_gbs, 4),
+            "tflops": round(flop * ne / (t * 1e-3) / 1e12, 2),
+            "fp32_alu_peak_tflops": round(fp32_peak, 1),
+            "alu_frac": round(flop * ne / (t * 1e-3) / 1e12 / fp32_peak, 4),
+            "fp32_ms": round(t32, 4), "fp32_gbs_algorithmic": round(bytes_32 * ne / (t32 * 1e-3) / 1e9, 1),
+            "fp32_tflops": round(flop * ne / (t32 * 1e-3) / 1e12, 2),
+            "speedup_vs_fp32": round(t32 / t, 4),
+            "max_abs_diff_vs_fp32_input": float(d.max()), "max_abs_fp32_result": float(scale),
+            "bytes_per_element": {"compressed": bytes_c, "fp32": bytes_32},
+            "data": "synthetic TGV initial state (Sec. 4.2), Euler flux rows, degree-3 hexes"}
+    if args.cpu_seconds > 0:
+        from oracle import oracle as O
+        rng = np.random.default_rng(0)
+        sel = np.sort(rng.choice(ne, size=min(ne, 256), replace=False))
+        Wh = W[:, :, torch.from_numpy(sel).to(dev)].cpu().numpy().view(np.uint64)
+        t0 = time.perf_counter()
+        ref = O.flux_divergence(O.PRIMARY, Wh, D.cpu().numpy(), ns, nv)
+        dt = time.perf_counter() - t0
+        got = out[:, :, torch.from_numpy(sel).to(dev)].cpu().numpy().astype(np.float64)
+        line["cpu_baseline"] = {"value": round(sel.size / dt, 1), "unit": "elements/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"{sel.size} random elements of the same mesh",
+                                "max_abs_diff_vs_gpu": float(np.abs(got - ref).max())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -601,6 +672,8 @@ def main():
         run_batched(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "fdiv":
+        run_fdiv(args)
     else:
         run_ivc(args)
 

@@ -226,6 +226,35 @@ ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t 
                        uint64_t *c, int64_t n, const ivc_launch_config *cfg,
                        ivc_stream_t stream);
 
+/* Divergence of a compressed flux: Algorithm 1 (Sec. 4; Table fr_nse, step
+ * 10) of the flux-reconstruction right-hand side.  For every element e and
+ * solution point k, and every equation p:
+ *     div(k, p, e) = sum_j sum_c D[c ns + j][k] * X(j, p, e)_c
+ * where X(j, p, e) = decompress(F(j, p, e)) is the 3-vector flux row of
+ * equation p at point j of element e (Sec. 2), and D the element's divergence
+ * operator.  Products and sums in FP32, order unspecified (error within the
+ * FP32 summation bound of the 3 ns terms).
+ *   F    device words, row (j, p) of element e at F[(j * nvars + p) * ld + e]
+ *        (element index fastest, ld >= ne).
+ *   D    device FP32, row-major (3 ns) x ns: D[(c * ns + j) * ns + k] is the
+ *        derivative along axis c (0, 1, 2 = x, y, z) of the basis function of
+ *        point j, evaluated at point k.
+ *   div  device FP32 output, (k, p, e) at div[(k * nvars + p) * ld_out + e],
+ *        ld_out >= ne; entries with e >= ne are not written.
+ * Limits: 1 <= ns <= 64 (hex elements up to degree 3), 1 <= nvars <= 5.
+ * Errors: IVC_ERR_ARG for sizes out of range or NULL pointers with ne > 0,
+ * IVC_ERR_ALIGN for F not 8-byte or D / div not 4-byte aligned. */
+ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
+                               int nvars, int64_t ne, const float *D, float *div,
+                               int64_t ld_out, ivc_stream_t stream);
+
+/* The same divergence from an uncompressed FP32 flux (the baseline of
+ * Algorithm 1): component c of row (j, p) of element e at
+ * F[((c * ns + j) * nvars + p) * ld + e].  Other arguments as above. */
+ivc_status ivc_f32_flux_divergence(const float *F, int64_t ld, int ns, int nvars, int64_t ne,
+                                   const float *D, float *div, int64_t ld_out,
+                                   ivc_stream_t stream);
+
 /* Frees the cached per-format tables on the current device. */
 ivc_status ivc_release_tables(void);
 

@@ -237,3 +237,30 @@ def error_stats(x, xh) -> dict:
     _L().ivco_error_stats(a.ctypes.data, b.ctypes.data, a.shape[0], ctypes.byref(s))
     return {k: (int(getattr(s, k)) if k == "n" else float(getattr(s, k)))
             for k, _ in _CStats._fields_}
+
+
+def flux_divergence(fmt: Format, w, D, ns: int, nvars: int) -> np.ndarray:
+    """Algorithm 1 (Sec. 4; Table fr_nse, step 10): divergence of a compressed flux.
+
+    ``w`` holds one word per flux row, (point j, row p, element e) at
+    ``w[j, p, e]`` (shape (ns, nvars, ne), or flat in that order); each row is
+    the 3-vector (F_x, F_y, F_z) of one equation at one solution point.
+    ``D`` is the (3 ns, ns) operator, ``D[c * ns + j, k]`` the derivative along
+    axis c of the basis function of point j at point k, given as FP32.
+
+    The steps follow the algorithm: for every element and solution point j,
+    decompress the point's rows to X (nvars x 3); for every point k, take
+    d = (D[j, k], D[j + ns, k], D[j + 2 ns, k]) and accumulate X d into the
+    divergence at (k, element).  Accumulation in FP64 (the loop over elements
+    is the array axis).  Returns float64 of shape (ns, nvars, ne)."""
+    ww = np.asarray(w, dtype=np.uint64).reshape(ns, nvars, -1)
+    ne = ww.shape[2]
+    X = decompress(fmt, ww.reshape(-1)).reshape(ns, nvars, ne, 3).astype(np.float64)
+    DD = np.asarray(D, dtype=np.float32).astype(np.float64).reshape(3 * ns, ns)
+    div = np.zeros((ns, nvars, ne), dtype=np.float64)
+    for j in range(ns):
+        Xj = X[j]
+        for k in range(ns):
+            d = np.array([DD[j, k], DD[j + ns, k], DD[j + 2 * ns, k]])
+            div[k] += Xj @ d
+    return div

@@ -1,6 +1,6 @@
 """Build the C-ABI shared library ``_build/libivc.so`` for sm_103a with nvcc.
 
-The three translation units compile in parallel; the result is loaded by
+The translation units compile in parallel; the result is loaded by
 ``ivc.py`` through ctypes.  Usage: ``python -m paper_2003_02633_gb300.build``.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libivc.so")
-SOURCES = ["ivc_ops.cu", "ivc_api.cu", "ivc_baseline.cu", "ivc_noalloc.cu"]
+SOURCES = ["ivc_ops.cu", "ivc_api.cu", "ivc_baseline.cu", "ivc_noalloc.cu", "ivc_fdiv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"]

@@ -476,6 +476,47 @@ ivc_status ivc_pointwise_update(const ivc_format *fmt, float dt, const uint64_t 
   return cuda_status(launch_update(map, F, dt, v, f, rho, v_out, m_out, n, s, stream));
 }
 
+// ---------------------------------------------------------- flux divergence
+
+namespace {
+
+ivc_status fdiv_args(const void *F, int64_t ld, int ns, int nvars, int64_t ne, const float *D,
+                     float *div, int64_t ld_out, size_t falign) {
+  if (ne < 0 || ns < 1 || ns > 64 || nvars < 1 || nvars > 5) return IVC_ERR_ARG;
+  if (ne == 0) return IVC_OK;
+  if (ld < ne || ld_out < ne || !F || !D || !div) return IVC_ERR_ARG;
+  if (!aligned(F, falign) || !aligned(D, 4) || !aligned(div, 4)) return IVC_ERR_ALIGN;
+  return IVC_OK;
+}
+
+}  // namespace
+
+ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
+                               int nvars, int64_t ne, const float *D, float *div,
+                               int64_t ld_out, ivc_stream_t stream) {
+  DevFormat Fm;
+  int map;
+  ivc_status st = ivc::format_fields(fmt, &Fm, &map);  // no device work yet
+  if (st != IVC_OK) return st;
+  st = fdiv_args(F, ld, ns, nvars, ne, D, div, ld_out, 8);
+  if (st != IVC_OK || ne == 0) return st;
+  st = make_devformat(fmt, &Fm, &map);
+  if (st != IVC_OK) return st;
+  const bool fastp = map == IVC_MAP_UNIFORM && fast::is_primary(Fm);
+  return cuda_status(launch_flux_div(map, fastp, false, Fm, F, ld, ns, nvars, ne, D, div, ld_out,
+                                     stream));
+}
+
+ivc_status ivc_f32_flux_divergence(const float *F, int64_t ld, int ns, int nvars, int64_t ne,
+                                   const float *D, float *div, int64_t ld_out,
+                                   ivc_stream_t stream) {
+  ivc_status st = fdiv_args(F, ld, ns, nvars, ne, D, div, ld_out, 4);
+  if (st != IVC_OK || ne == 0) return st;
+  DevFormat none{};
+  return cuda_status(launch_flux_div(IVC_MAP_UNIFORM, false, true, none, F, ld, ns, nvars, ne, D,
+                                     div, ld_out, stream));
+}
+
 // ------------------------------------------------------------------ batched
 
 struct ivc_plan_s {

@@ -92,6 +92,12 @@ cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P
 cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,
                              cudaStream_t st);
 
+// Divergence of a compressed (or, with f32, an FP32) flux, Algorithm 1; the
+// launcher sizes its own grid (SMs x resident blocks, capped by the tiles).
+cudaError_t launch_flux_div(int map, bool fast_path, bool f32, const DevFormat &F,
+                            const void *src, int64_t ld, int ns, int nv, int64_t ne,
+                            const float *D, float *div, int64_t ld_out, cudaStream_t st);
+
 // Resident blocks per SM of a kernel at a block size (0 if it cannot run).
 int occupancy(int map, int kind, int block, size_t smem);
 

@@ -84,6 +84,8 @@ _SIGS = {
     "ivc_plan_destroy": [_P],
     "ivc_tune": [_FMT, _I, _P, _P, _P, _I64, _P, ctypes.POINTER(ivc_launch_config)],
     "ivc_add_noalloc": [_FMT, _P, _P, _P, _I64, _P],
+    "ivc_flux_divergence": [_FMT, _P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
+    "ivc_f32_flux_divergence": [_P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
 }
 EXPORTS = sorted(list(_SIGS) + ["ivc_status_string", "ivc_version"])
 
@@ -194,6 +196,36 @@ def add(fmt, a, b, out=None, cfg=None, stream=None):
     c = ctypes.byref(cfg) if cfg is not None else None
     _chk(load().ivc_add_cfg(ctypes.byref(fmt), _ptr(a), _ptr(b), _ptr(out), a.shape[0], c,
                             _stream(stream)), "ivc_add")
+    return out
+
+
+def flux_divergence(fmt, F, D, ne=None, out=None, stream=None):
+    """Algorithm 1: divergence of a compressed flux.  F: int64 words of shape
+    (ns, nvars, ld) (element index fastest; the first ``ne`` elements are
+    used, default all); D: float32 (3 ns, ns).  Returns float32
+    (ns, nvars, ld_out) with ld_out = out.shape[2] (default ld)."""
+    import torch
+    ns, nv, ld = F.shape
+    ne = ld if ne is None else int(ne)
+    if out is None:
+        out = torch.empty((ns, nv, ld), dtype=torch.float32, device=F.device)
+    _chk(load().ivc_flux_divergence(ctypes.byref(fmt), _ptr(F), ld, ns, nv, ne, _ptr(D),
+                                    _ptr(out), out.shape[2], _stream(stream)),
+         "ivc_flux_divergence")
+    return out
+
+
+def f32_flux_divergence(F, D, ne=None, out=None, stream=None):
+    """Algorithm 1 on an uncompressed flux: F float32 of shape (3, ns, nvars, ld)
+    (component c of row (j, p) of element e at F[c, j, p, e])."""
+    import torch
+    _, ns, nv, ld = F.shape
+    ne = ld if ne is None else int(ne)
+    if out is None:
+        out = torch.empty((ns, nv, ld), dtype=torch.float32, device=F.device)
+    _chk(load().ivc_f32_flux_divergence(_ptr(F), ld, ns, nv, ne, _ptr(D), _ptr(out),
+                                        out.shape[2], _stream(stream)),
+         "ivc_f32_flux_divergence")
     return out
 
 

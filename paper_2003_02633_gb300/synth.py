@@ -277,3 +277,76 @@ def tgv_fields_device(elements_per_axis: int, device, order: int = 3, p0: float 
                      dim=1) / rho[:, None]
     vel = torch.stack([u, v, w], dim=1)
     return vel.float().contiguous(), f.float().contiguous(), rho.float().contiguous()
+
+
+def fr_hex_operator(order: int = 3, h: float = 1.0) -> np.ndarray:
+    """Divergence operator of a flux-reconstruction hex element (Sec. 4,
+    Algorithm 1): D[c * ns + j, k] = d l_j / d x_c at solution point k, with
+    l_j the tensor-product Lagrange basis on the (order+1)^3 Gauss-Legendre
+    points of a cube of side h (reference [-1, 1]^3, scaled by 2 / h).
+    Point j = (jz q + jy) q + jx, q = order + 1.  Returns float32 (3 ns, ns)."""
+    q = order + 1
+    xg, _ = np.polynomial.legendre.leggauss(q)
+    # 1-D derivative matrix L[b, a] = l_b'(xi_a)
+    L = np.zeros((q, q))
+    for b in range(q):
+        others = np.delete(xg, b)
+        coef = np.polynomial.polynomial.polyfromroots(others) / np.prod(xg[b] - others)
+        L[b] = np.polynomial.polynomial.polyval(xg, np.polynomial.polynomial.polyder(coef))
+    ns = q ** 3
+    D = np.zeros((3 * ns, ns))
+    eye = np.eye(q)
+    for j in range(ns):
+        jz, jy, jx = j // (q * q), (j // q) % q, j % q
+        for k in range(ns):
+            kz, ky, kx = k // (q * q), (k // q) % q, k % q
+            D[0 * ns + j, k] = L[jx, kx] * eye[jy, ky] * eye[jz, kz]
+            D[1 * ns + j, k] = eye[jx, kx] * L[jy, ky] * eye[jz, kz]
+            D[2 * ns + j, k] = eye[jx, kx] * eye[jy, ky] * L[jz, kz]
+    return (D * (2.0 / h)).astype(np.float32)
+
+
+def tgv_euler_flux(elements_per_axis: int = 96, order: int = 3, p0: float = 100.0,
+                   rho0: float = 1.0, u0: float = 1.0, gamma: float = 1.4, device="cpu",
+                   elements=None):
+    """Inviscid (Euler) flux of the Taylor-Green vortex initial state (Sec. 4.2,
+    Eq. tgv_xyz, k = 1) at the (order+1)^3 Gauss-Legendre solution points of the
+    hex elements of a uniform mesh on [-pi, pi]^3, as the five flux rows of the
+    conserved variables: rho u, rho u u + p e_x, rho u v + p e_y, rho u w + p e_z,
+    (E + p) u with E = p / (gamma - 1) + rho |u|^2 / 2 and rho = p rho0 / p0.
+
+    Layout for the divergence kernel: float32 torch tensor (ns, 5, ne, 3),
+    element index fastest; element e = (ez E + ey) E + ex.  ``elements`` limits
+    the count to the first ones (tests).  Computed in FP64 on ``device``."""
+    import torch
+    q = order + 1
+    ns = q ** 3
+    E = elements_per_axis
+    ne = E ** 3 if elements is None else int(elements)
+    xg, _ = np.polynomial.legendre.leggauss(q)
+    h = 2.0 * math.pi / E
+    dev = torch.device(device)
+    e = torch.arange(ne, device=dev, dtype=torch.int64)
+    ez, ey, ex = e // (E * E), (e // E) % E, e % E
+    xgt = torch.tensor(xg, device=dev, dtype=torch.float64)
+    out = torch.empty((ns, 5, ne, 3), device=dev, dtype=torch.float32)
+    c = rho0 * u0 * u0 / 16.0
+    for j in range(ns):
+        jz, jy, jx = j // (q * q), (j // q) % q, j % q
+        X = -math.pi + h * (ex.double() + 0.5) + 0.5 * h * xgt[jx]
+        Y = -math.pi + h * (ey.double() + 0.5) + 0.5 * h * xgt[jy]
+        Z = -math.pi + h * (ez.double() + 0.5) + 0.5 * h * xgt[jz]
+        u = u0 * torch.sin(X) * torch.cos(Y) * torch.cos(Z)
+        v = -u0 * torch.cos(X) * torch.sin(Y) * torch.cos(Z)
+        w = torch.zeros_like(u)
+        p = p0 + c * (torch.cos(2 * X) + torch.cos(2 * Y)) * (2 + torch.cos(2 * Z))
+        rho = p * rho0 / p0
+        Et = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+        vel = torch.stack([u, v, w], dim=1)
+        rows = [rho[:, None] * vel,
+                rho[:, None] * u[:, None] * vel + torch.stack([p, 0 * p, 0 * p], dim=1),
+                rho[:, None] * v[:, None] * vel + torch.stack([0 * p, p, 0 * p], dim=1),
+                rho[:, None] * w[:, None] * vel + torch.stack([0 * p, 0 * p, p], dim=1),
+                (Et + p)[:, None] * vel]
+        out[j] = torch.stack(rows, dim=0).to(torch.float32)
+    return out

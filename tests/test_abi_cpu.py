@@ -79,6 +79,18 @@ def test_argument_errors_before_device_work(lib):
     assert lib.ivc_f32_add(1, None, None, None, 2, 5, None) == ivc.IVC_ERR_ARG  # ld < n
     assert lib.ivc_half_add(9, None, None, None, 1, None) == ivc.IVC_ERR_ARG
     assert lib.ivc_error_stats(None, None, -1, None, None) == ivc.IVC_ERR_ARG
+    # flux divergence: sizes out of range, ld < ne, NULL pointers, empty call
+    fd = lib.ivc_flux_divergence
+    assert fd(ctypes.byref(f), None, 0, 0, 5, 1, None, None, 1, None) == ivc.IVC_ERR_ARG
+    assert fd(ctypes.byref(f), None, 0, 65, 5, 1, None, None, 1, None) == ivc.IVC_ERR_ARG
+    assert fd(ctypes.byref(f), None, 0, 64, 6, 1, None, None, 1, None) == ivc.IVC_ERR_ARG
+    assert fd(ctypes.byref(f), None, 0, 64, 5, 2, None, None, 2, None) == ivc.IVC_ERR_ARG
+    assert fd(ctypes.byref(f), None, 0, 64, 5, 0, None, None, 0, None) == ivc.IVC_OK
+    assert fd(ctypes.byref(bad), None, 0, 64, 5, 0, None, None, 0, None) == ivc.IVC_ERR_FORMAT
+    f32fd = lib.ivc_f32_flux_divergence
+    assert f32fd(None, 4, 64, 5, 4, None, None, 4, None) == ivc.IVC_ERR_ARG
+    assert f32fd(None, 0, 64, 5, -1, None, None, 0, None) == ivc.IVC_ERR_ARG
+    assert f32fd(None, 0, 64, 5, 0, None, None, 0, None) == ivc.IVC_OK
     ws = ctypes.c_size_t(0)
     assert lib.ivc_plan_batched(ctypes.byref(f), 0, None, 0, None, ctypes.byref(ws), None, None,
                                 None) == ivc.IVC_ERR_ARG
