@@ -86,6 +86,7 @@ _SIGS = {
     "ivc_add_noalloc": [_FMT, _P, _P, _P, _I64, _P],
     "ivc_flux_divergence": [_FMT, _P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
     "ivc_f32_flux_divergence": [_P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
+    "ivc_add_host": [_FMT, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P],
 }
 EXPORTS = sorted(list(_SIGS) + ["ivc_status_string", "ivc_version"])
 
@@ -226,6 +227,21 @@ def f32_flux_divergence(F, D, ne=None, out=None, stream=None):
     _chk(load().ivc_f32_flux_divergence(_ptr(F), ld, ns, nv, ne, _ptr(D), _ptr(out),
                                         out.shape[2], _stream(stream)),
          "ivc_f32_flux_divergence")
+    return out
+
+
+def add_host(fmt, a, b, out, workspace, stream=None):
+    """ivc_add_host: c = a + b for int64 word tensors in (pinned) host memory,
+    streamed through the device tensor ``workspace`` (any dtype, 16-byte
+    aligned) in chunks.  Asynchronous on ``stream``: synchronise before reading
+    ``out``."""
+    for t in (a, b, out):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("add_host expects contiguous host tensors")
+    _chk(load().ivc_add_host(ctypes.byref(fmt), a.data_ptr(), b.data_ptr(), out.data_ptr(),
+                             a.shape[0], _ptr(workspace),
+                             workspace.numel() * workspace.element_size(), _stream(stream)),
+         "ivc_add_host")
     return out
 
 

@@ -87,6 +87,14 @@ def test_argument_errors_before_device_work(lib):
     assert fd(ctypes.byref(f), None, 0, 64, 5, 2, None, None, 2, None) == ivc.IVC_ERR_ARG
     assert fd(ctypes.byref(f), None, 0, 64, 5, 0, None, None, 0, None) == ivc.IVC_OK
     assert fd(ctypes.byref(bad), None, 0, 64, 5, 0, None, None, 0, None) == ivc.IVC_ERR_FORMAT
+    ah = lib.ivc_add_host
+    assert ah(ctypes.byref(f), None, None, None, -1, None, 0, None) == ivc.IVC_ERR_ARG
+    assert ah(ctypes.byref(f), None, None, None, 0, None, 0, None) == ivc.IVC_OK
+    assert ah(ctypes.byref(f), None, None, None, 4, None, 0, None) == ivc.IVC_ERR_ARG
+    assert ah(ctypes.byref(bad), None, None, None, 4, None, 0, None) == ivc.IVC_ERR_FORMAT
+    buf = (ctypes.c_uint64 * 16)()
+    p16 = (ctypes.addressof(buf) + 15) & ~15   # a 16-byte aligned workspace of 64 bytes
+    assert ah(ctypes.byref(f), buf, buf, buf, 4, p16, 64, None) == ivc.IVC_ERR_NOMEM
     f32fd = lib.ivc_f32_flux_divergence
     assert f32fd(None, 4, 64, 5, 4, None, None, 4, None) == ivc.IVC_ERR_ARG
     assert f32fd(None, 0, 64, 5, -1, None, None, 0, None) == ivc.IVC_ERR_ARG

@@ -311,3 +311,39 @@ def test_tune_returns_a_valid_shape():
     with np.errstate(invalid="ignore", over="ignore"):
         pre = O.decompress(fo, O.compress(fo, a)) + O.decompress(fo, O.compress(fo, b))
     check_words(fo, pre, _host_words(out), want, "add tuned")
+
+
+@pytest.mark.parametrize("ws_vectors", [1000, 1 << 16])
+def test_add_host_streams_chunks(c0, ws_vectors):
+    """ivc_add_host: host words through a device workspace of a few chunks
+    (ragged last chunk, more chunks than slots) give the oracle's words."""
+    fo, fg = formats("primary")
+    wa, wb = O.compress(fo, c0[0]), O.compress(fo, c0[1])
+    n = wa.shape[0]
+    ha = torch.from_numpy(wa.view(np.int64)).pin_memory()
+    hb = torch.from_numpy(wb.view(np.int64)).pin_memory()
+    hc = torch.zeros(n, dtype=torch.int64).pin_memory()
+    ws = torch.empty(3 * 3 * ws_vectors, dtype=torch.int64, device=DEV)
+    ivc.add_host(fg, ha, hb, hc, ws)
+    torch.cuda.synchronize()
+    got = hc.numpy().view(np.uint64)
+    exp = O.add(fo, wa, wb)
+    dev = _host_words(ivc.add(fg, _words_dev(wa), _words_dev(wb)))
+    assert np.array_equal(got, dev)
+    mism = int(np.sum(got != exp))
+    assert mism <= allowed_mismatches(n)
+
+
+def test_add_host_tiny_chunks():
+    fo, fg = formats("primary")
+    a, b = synth.roundtrip_inputs(101, seed=5)
+    wa, wb = O.compress(fo, a), O.compress(fo, b)
+    n = wa.shape[0]
+    ha = torch.from_numpy(wa.view(np.int64))           # pageable memory also works
+    hb = torch.from_numpy(wb.view(np.int64))
+    hc = torch.zeros(n, dtype=torch.int64)
+    ws = torch.empty(3 * 3 * 2, dtype=torch.int64, device=DEV)   # chunks of 2 vectors
+    ivc.add_host(fg, ha, hb, hc, ws)
+    torch.cuda.synchronize()
+    got = hc.numpy().view(np.uint64)
+    assert int(np.sum(got != O.add(fo, wa, wb))) <= allowed_mismatches(n)
