@@ -16,7 +16,6 @@ on bounded samples of the same workload.
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import math
@@ -56,9 +55,11 @@ def parse_args():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the compressed add kernel and its launch
+    (the committed DRAM-traffic figure is valid only for that exact code)."""
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2003_02633_gb300", "csrc", "*")))
-    files.append(os.path.join(ROOT, "include", "ivc.h"))
+    csrc = os.path.join(ROOT, "paper_2003_02633_gb300", "csrc")
+    files = [os.path.join(csrc, f) for f in ("ivc_device.cuh", "ivc_fast.cuh", "ivc_ops.cu")]
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
@@ -356,6 +357,22 @@ def run_extras(args, fmt, a, b, wa, wb, stream, s_handle, n, pg, dev, value):
     ms, _ = t(lambda: ivc.compress(fmt, a, out=cw, stream=s_handle))
     out["compress_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
     del d, cw
+    # the paper's other layouts and variants, same vectors (Sec. 2.3-2.5)
+    variants = {"L1717": dict(exp_bits=7, man_bits=23, phi_bits=17, theta_bits=17, exp_bias=80),
+                "L1617": dict(exp_bits=8, man_bits=23, phi_bits=16, theta_bits=17,
+                              exp_bias=127),
+                "fracsplit": dict(map=2, nphi_max_p1=185363),
+                "tanh": dict(map=1, gamma=0.5)}
+    va, vb = torch.empty_like(wa), torch.empty_like(wb)
+    for name, kw in variants.items():
+        f = ivc.make_format(**kw)
+        ivc.compress(f, a, out=va, stream=s_handle)
+        ivc.compress(f, b, out=vb, stream=s_handle)
+        vc = torch.empty_like(va)
+        ms, _ = t(lambda: ivc.add(f, va, vb, out=vc, stream=s_handle))
+        out[f"add_{name}_gvec_s"] = round(n / (ms * 1e-3) / 1e9, 4)
+        del vc
+    del va, vb
     torch.cuda.synchronize()
     return out
 
@@ -624,6 +641,7 @@ def run_fdiv(args):
                             warmup, stream)
     ms32, per32 = time_launches(lambda: ivc.f32_flux_divergence(Fc, D, out=out32, stream=s),
                                 steps, warmup, stream)
+    ivc.flux_divergence_check()
     t, t32 = ms / steps, ms32 / steps
     flop = 2.0 * 3 * ns * ns * nv                                   # per element
     bytes_c = ns * nv * 8 + ns * nv * 4

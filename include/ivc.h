@@ -248,6 +248,13 @@ ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t
                                int nvars, int64_t ne, const float *D, float *div,
                                int64_t ld_out, ivc_stream_t stream);
 
+/* Reports (and clears) a failure of the flux-divergence kernels since the
+ * last check: their decoding and accumulating warps hand shared-memory
+ * buffers to each other through barriers whose waits are bounded (about a
+ * second); a wait that runs out ends the launch early and is reported here as
+ * IVC_ERR_TIMEOUT.  Synchronises with the current device.  IVC_OK otherwise. */
+ivc_status ivc_flux_divergence_check(void);
+
 /* The same divergence from an uncompressed FP32 flux (the baseline of
  * Algorithm 1): component c of row (j, p) of element e at
  * F[((c * ns + j) * nvars + p) * ld + e].  Other arguments as above. */

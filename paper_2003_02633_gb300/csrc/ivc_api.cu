@@ -507,6 +507,15 @@ ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t
                                      stream));
 }
 
+ivc_status ivc_flux_divergence_check(void) {
+  int status = 0;
+  if (flux_div_status(&status) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  return status ? IVC_ERR_TIMEOUT : IVC_OK;
+}
+
 ivc_status ivc_f32_flux_divergence(const float *F, int64_t ld, int ns, int nvars, int64_t ne,
                                    const float *D, float *div, int64_t ld_out,
                                    ivc_stream_t stream) {

@@ -3,57 +3,245 @@
 //     div(k, p) = sum_j sum_c D[c ns + j][k] X(j, p)_c,   X = decompress(F).
 //
 // GB300 layout of the work: a block owns a tile of 64 elements and all ns
-// output points.  Solution points j are taken in chunks of 8: the block first
-// decodes the chunk's words (8 points x nvars rows x 64 elements, coalesced
-// along the element index) into shared memory as FP32, then every thread
-// accumulates a 4 (points k) x nvars x 4 (elements) block of the output from
-// the chunk with FP32 FMAs, reading D (staged once per block) and the decoded
-// flux from shared memory.  The contraction has K = 3 ns = 192 terms per
-// output for hex elements of degree 3; it runs on the FP32 pipes because its
-// operands carry 24-bit significands and the result is compared with an FP32
-// summation bound (a TF32 or BF16 tensor-core product would round the decoded
-// flux to 11 or 8 bits).
+// output points, and splits its warps by role.  Eight producer warps take the
+// words of 8 solution points at a time (8 x nvars rows x 64 elements,
+// coalesced along the element index): they copy the next chunk's words into
+// shared memory with asynchronous copies (cp.async) while decoding the current
+// chunk's words into one of two shared-memory buffers as FP32.  Eight
+// consumer warps accumulate, per thread, a 4 (points k) x nvars x 4
+// (elements) block of the output with FP32 FMAs from the other buffer and
+// from D (staged once per block).  Two mbarriers per buffer ("full": the
+// producers' arrivals, "empty": the consumers') hand the buffers back and
+// forth, so decoding the next points overlaps the FMAs of the current ones,
+// and the 80 accumulators never share a thread with the decoder's registers.
+// Every wait is bounded (about a second of clock cycles); a wait that runs
+// out marks the launch failed in a device status word and the block leaves.
+//
+// The contraction has K = 3 ns = 192 terms per output for hex elements of
+// degree 3; it runs on the FP32 pipes because its operands carry 24-bit
+// significands and the result is held to an FP32 summation bound (a TF32 or
+// BF16 tensor-core product would round the decoded flux to 11 or 8 bits).
 #include "ivc_internal.h"
 
 namespace ivc {
 namespace {
 
-constexpr int kTE = 64;       // elements per tile
-constexpr int kJC = 8;        // solution points per chunk
+constexpr int kTE = 64;         // elements per tile
+constexpr int kJC = 8;          // solution points per chunk
 constexpr int kMaxNs = 64;
 constexpr int kMaxNv = 5;
-constexpr int kThreads = 256;
+constexpr int kProducers = 256; // 8 warps
+constexpr int kConsumers = 256; // 8 warps
+constexpr int kThreads = kProducers + kConsumers;
+constexpr int kXBuf = kJC * kMaxNv * 3 * kTE;   // floats per decoded buffer
+constexpr int kWBuf = kJC * kMaxNv * kTE * 3;   // 32-bit units per raw buffer (FP32 rows)
+constexpr long long kWaitCycles = 2000000000ll; // about a second
 
 enum : int { FD_GENERIC = 0, FD_FAST = 1, FD_F32 = 2 };
 
+__device__ int g_fdiv_status;  // 0 ok, 1 a bounded wait ran out
+
 __host__ __device__ constexpr int pad4(int v) { return (v + 3) & ~3; }
 
-// Shared memory: [tables][D: 3 ns x pad4(ns)][X: kJC x nvars x 3 x kTE]
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+// 4- or 8-byte asynchronous global-to-shared copy; bytes = 0 fills zeros
+// without reading the source.
+template <int SIZE>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_addr(dst)),
+               "l"(__cvta_generic_to_global(src)), "n"(SIZE), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_1() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// Waits for the completion of the barrier phase with the given parity;
+// false when about a second of cycles passed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+// Copies the raw data of one chunk (words, or FP32 components) into a raw
+// buffer: item q (two adjacent elements of row (jj, p)) at q * 2 words, or at
+// q * 6 floats (component-major pairs).  Each producer thread copies exactly
+// the items it decodes later, so only its own cp.async groups need waiting.
+template <int MODE>
+__device__ __forceinline__ void copy_chunk(uint32_t *Wb, const void *src, int64_t ld, int ns,
+                                           int nv, int64_t ne, int64_t e0, int j0, int jn,
+                                           int pt) {
+  const int items = jn * nv * (kTE / 2);
+  for (int q = pt; q < items; q += kProducers) {
+    const int e2 = q & (kTE / 2 - 1);
+    const int r = q / (kTE / 2);
+    const int jj = r / nv, p = r - jj * nv;
+    const int64_t e = e0 + 2 * e2;
+    if (MODE == FD_F32) {
+      const float *Fr = static_cast<const float *>(src);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int64_t base = (((int64_t)c * ns + j0 + jj) * nv + p) * ld + e;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const bool in = e + t < ne;
+          cp_async<4>(Wb + q * 6 + c * 2 + t, in ? (const void *)(Fr + base + t) : src,
+                      in ? 4u : 0u);
+        }
+      }
+    } else {
+      const uint64_t *W = static_cast<const uint64_t *>(src);
+      const int64_t base = ((int64_t)(j0 + jj) * nv + p) * ld + e;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const bool in = e + t < ne;
+        cp_async<8>(Wb + (q * 2 + t) * 2, in ? (const void *)(W + base + t) : src, in ? 8u : 0u);
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+// Shared memory: [tables][D: 3 ns x pad4(ns)][X: 2 x kXBuf][raw: 2 x kWBuf]
+//                [full[2], empty[2]][abort]
 template <int MODE, int MAP>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     k_flux_div(const __grid_constant__ DevFormat F, const void *__restrict__ src, int64_t ld,
                int ns, int nv, int64_t ne, const float *__restrict__ D, float *__restrict__ div,
                int64_t ld_out) {
   extern __shared__ __align__(16) unsigned char fd_smem[];
   TabEntry *tabs = reinterpret_cast<TabEntry *>(fd_smem);
   const int ntab = (MODE == FD_F32 || MAP == MAP_TANH) ? 0 : F.nent_t + F.nent_p;
-  if (ntab > 0) stage_tables<MAP>(F, tabs);
-  const TabEntry *tab_t = tabs;
-  const TabEntry *tab_p = tabs + (MAP == MAP_TANH ? 0 : F.nent_t);
   const int nsp = pad4(ns);
   float *Ds = reinterpret_cast<float *>(fd_smem + (size_t)ntab * sizeof(TabEntry));
   float *Xs = Ds + 3 * ns * nsp;
-  // D once per block, rows padded to a multiple of 4 columns
+  uint32_t *Ws = reinterpret_cast<uint32_t *>(Xs + 2 * kXBuf);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(Ws + 2 * kWBuf);  // full[0..1], empty[0..1]
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 4);
+
+  if (ntab > 0) stage_tables<MAP>(F, tabs);
+  const TabEntry *tab_t = tabs;
+  const TabEntry *tab_p = tabs + (MAP == MAP_TANH ? 0 : F.nent_t);
   for (int i = threadIdx.x; i < 3 * ns * nsp; i += kThreads) {
     const int r = i / nsp, k = i - r * nsp;
     Ds[i] = k < ns ? D[(int64_t)r * ns + k] : 0.0f;
   }
+  if (threadIdx.x == 0) {
+    mbar_init(bars + 0, kProducers);
+    mbar_init(bars + 1, kProducers);
+    mbar_init(bars + 2, kConsumers);
+    mbar_init(bars + 3, kConsumers);
+    *abort_flag = 0;
+  }
   __syncthreads();
 
-  const int eg = threadIdx.x & 15;   // elements 4 eg .. 4 eg + 3 of the tile
-  const int kg = threadIdx.x >> 4;   // points 4 kg .. 4 kg + 3
-  const bool kact = 4 * kg < nsp;
   const int64_t ntiles = (ne + kTE - 1) / kTE;
+  const int nchunk = (ns + kJC - 1) / kJC;
+
+  if (threadIdx.x < kProducers) {
+    // ------------------------------------------------------------ producers
+    const int pt = threadIdx.x;
+    uint32_t g = 0;
+    int64_t tile = blockIdx.x;
+    int ch = 0;
+    if (tile < ntiles)
+      copy_chunk<MODE>(Ws, src, ld, ns, nv, ne, tile * kTE, 0, min(kJC, ns), pt);
+    while (tile < ntiles) {
+      // start the copies of the next chunk, then wait for this chunk's
+      int64_t ntile = tile;
+      int nch = ch + 1;
+      if (nch == nchunk) {
+        nch = 0;
+        ntile += gridDim.x;
+      }
+      if (ntile < ntiles)
+        copy_chunk<MODE>(Ws + ((g + 1) & 1) * kWBuf, src, ld, ns, nv, ne, ntile * kTE,
+                         nch * kJC, min(kJC, ns - nch * kJC), pt);
+      else
+        cp_async_commit();  // an empty group keeps "all but the newest" meaning this chunk
+      cp_async_wait_1();
+      const int b = g & 1;
+      const uint32_t u = g >> 1;
+      if (u >= 1 && !mbar_wait(bars + 2 + b, (u - 1) & 1u)) {
+        *abort_flag = 1;
+        atomicExch(&g_fdiv_status, 1);
+        return;
+      }
+      if (*abort_flag) return;
+      const int jn = min(kJC, ns - ch * kJC);
+      float *X = Xs + b * kXBuf;
+      const uint32_t *Wb = Ws + b * kWBuf;
+      const int items = jn * nv * (kTE / 2);
+      for (int q = pt; q < items; q += kProducers) {
+        const int e2 = q & (kTE / 2 - 1);
+        const int r = q / (kTE / 2);
+        const int jj = r / nv, p = r - jj * nv;
+        float2 vx, vy, vz;
+        if (MODE == FD_F32) {
+          vx = *reinterpret_cast<const float2 *>(Wb + q * 6);
+          vy = *reinterpret_cast<const float2 *>(Wb + q * 6 + 2);
+          vz = *reinterpret_cast<const float2 *>(Wb + q * 6 + 4);
+        } else {
+          const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(Wb + q * 4);
+          if (MODE == FD_FAST) {
+            fast::decode2_full(w.x, w.y, F, tab_t, tab_p, vx, vy, vz);
+          } else {
+            const float3 a = decode_word<MAP>(w.x, F, tab_t, tab_p);
+            const float3 c3 = decode_word<MAP>(w.y, F, tab_t, tab_p);
+            vx = make_float2(a.x, c3.x);
+            vy = make_float2(a.y, c3.y);
+            vz = make_float2(a.z, c3.z);
+          }
+        }
+        float *xr = X + ((jj * kMaxNv + p) * 3) * kTE + 2 * e2;
+        *reinterpret_cast<float2 *>(xr) = vx;
+        *reinterpret_cast<float2 *>(xr + kTE) = vy;
+        *reinterpret_cast<float2 *>(xr + 2 * kTE) = vz;
+      }
+      mbar_arrive(bars + b);
+      tile = ntile;
+      ch = nch;
+      ++g;
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int ct = threadIdx.x - kProducers;
+  const int eg = ct & 15;   // elements 4 eg .. 4 eg + 3 of the tile
+  const int kg = ct >> 4;   // points 4 kg .. 4 kg + 3
+  const bool kact = 4 * kg < nsp;
+  uint32_t g = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kTE;
     float acc[4][kMaxNv][4];
@@ -62,52 +250,19 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int p = 0; p < kMaxNv; ++p)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][p][b] = 0.0f;
-
-    for (int j0 = 0; j0 < ns; j0 += kJC) {
-      const int jn = min(kJC, ns - j0);
-      __syncthreads();  // the previous chunk's readers are done with Xs
-      // decode: jn x nv rows x 64 elements, two adjacent elements per item
-      const int items = jn * nv * (kTE / 2);
-      for (int q = threadIdx.x; q < items; q += kThreads) {
-        const int e2 = q & (kTE / 2 - 1);
-        const int r = q / (kTE / 2);
-        const int jj = r / nv, p = r - jj * nv;
-        const int64_t e = e0 + 2 * e2;
-        float2 vx, vy, vz;
-        if (MODE == FD_F32) {
-          const float *Fr = static_cast<const float *>(src);
-          float v[3][2];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const int64_t base = (((int64_t)c * ns + j0 + jj) * nv + p) * ld + e;
-            v[c][0] = e < ne ? __ldcs(Fr + base) : 0.0f;
-            v[c][1] = e + 1 < ne ? __ldcs(Fr + base + 1) : 0.0f;
-          }
-          vx = make_float2(v[0][0], v[0][1]);
-          vy = make_float2(v[1][0], v[1][1]);
-          vz = make_float2(v[2][0], v[2][1]);
-        } else {
-          const uint64_t *W = static_cast<const uint64_t *>(src);
-          const int64_t base = ((int64_t)(j0 + jj) * nv + p) * ld + e;
-          const uint64_t w0 = e < ne ? __ldcs(W + base) : 0ull;
-          const uint64_t w1 = e + 1 < ne ? __ldcs(W + base + 1) : 0ull;
-          if (MODE == FD_FAST) {
-            fast::decode2_full(w0, w1, F, tab_t, tab_p, vx, vy, vz);
-          } else {
-            const float3 a = decode_word<MAP>(w0, F, tab_t, tab_p);
-            const float3 b = decode_word<MAP>(w1, F, tab_t, tab_p);
-            vx = make_float2(a.x, b.x);
-            vy = make_float2(a.y, b.y);
-            vz = make_float2(a.z, b.z);
-          }
-        }
-        float *xr = Xs + ((jj * kMaxNv + p) * 3) * kTE + 2 * e2;
-        *reinterpret_cast<float2 *>(xr) = vx;
-        *reinterpret_cast<float2 *>(xr + kTE) = vy;
-        *reinterpret_cast<float2 *>(xr + 2 * kTE) = vz;
+        for (int bb = 0; bb < 4; ++bb) acc[a][p][bb] = 0.0f;
+    for (int ch = 0; ch < nchunk; ++ch, ++g) {
+      const int b = g & 1;
+      const uint32_t u = g >> 1;
+      if (!mbar_wait(bars + b, u & 1u)) {
+        *abort_flag = 1;
+        atomicExch(&g_fdiv_status, 1);
+        return;
       }
-      __syncthreads();
+      if (*abort_flag) return;
+      const int j0 = ch * kJC;
+      const int jn = min(kJC, ns - j0);
+      const float *X = Xs + b * kXBuf;
       if (kact) {
         for (int jj = 0; jj < jn; ++jj) {
 #pragma unroll
@@ -119,19 +274,21 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int p = 0; p < kMaxNv; ++p) {
               if (p < nv) {
                 const float4 x = *reinterpret_cast<const float4 *>(
-                    Xs + ((jj * kMaxNv + p) * 3 + c) * kTE + 4 * eg);
+                    X + ((jj * kMaxNv + p) * 3 + c) * kTE + 4 * eg);
                 const float xe[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                  for (int b = 0; b < 4; ++b) acc[a][p][b] = fmaf(dk[a], xe[b], acc[a][p][b]);
+                  for (int bb = 0; bb < 4; ++bb)
+                    acc[a][p][bb] = fmaf(dk[a], xe[bb], acc[a][p][bb]);
               }
             }
           }
         }
       }
+      mbar_arrive(bars + 2 + b);
     }
-    // epilogue: points 4 kg + a < ns, elements e0 + 4 eg + b < ne
+    // epilogue: points 4 kg + a < ns, elements e0 + 4 eg + bb < ne
     if (kact) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -147,8 +304,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                    make_float4(acc[a][p][0], acc[a][p][1], acc[a][p][2], acc[a][p][3]));
           } else {
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-              if (e + b < ne) o[b] = acc[a][p][b];
+            for (int bb = 0; bb < 4; ++bb)
+              if (e + bb < ne) o[bb] = acc[a][p][bb];
           }
         }
       }
@@ -162,7 +319,8 @@ cudaError_t launch_one(const DevFormat &F, const void *src, int64_t ld, int ns, 
   const int ntab = (MODE == FD_F32 || MAP == MAP_TANH) ? 0 : F.nent_t + F.nent_p;
   const size_t smem = (size_t)ntab * sizeof(TabEntry) +
                       (size_t)(3 * ns * pad4(ns)) * sizeof(float) +
-                      (size_t)kJC * kMaxNv * 3 * kTE * sizeof(float);
+                      (size_t)2 * kXBuf * sizeof(float) + (size_t)2 * kWBuf * sizeof(uint32_t) +
+                      4 * sizeof(uint64_t) + 16;
   const void *k = (const void *)k_flux_div<MODE, MAP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -198,6 +356,13 @@ cudaError_t launch_flux_div(int map, bool fast_path, bool f32, const DevFormat &
     default:
       return launch_one<FD_GENERIC, MAP_FRACSPLIT>(F, src, ld, ns, nv, ne, D, div, ld_out, st);
   }
+}
+
+cudaError_t flux_div_status(int *status) {
+  cudaError_t e = cudaMemcpyFromSymbol(status, g_fdiv_status, sizeof(int));
+  if (e != cudaSuccess) return e;
+  const int zero = 0;
+  return cudaMemcpyToSymbol(g_fdiv_status, &zero, sizeof(int));
 }
 
 }  // namespace ivc

@@ -98,6 +98,10 @@ cudaError_t launch_flux_div(int map, bool fast_path, bool f32, const DevFormat &
                             const void *src, int64_t ld, int ns, int nv, int64_t ne,
                             const float *D, float *div, int64_t ld_out, cudaStream_t st);
 
+// Reads and clears the flux-divergence kernels' device status word (1: a
+// bounded wait between the decoding and the accumulating warps ran out).
+cudaError_t flux_div_status(int *status);
+
 // Resident blocks per SM of a kernel at a block size (0 if it cannot run).
 int occupancy(int map, int kind, int block, size_t smem);
 

@@ -87,6 +87,7 @@ _SIGS = {
     "ivc_flux_divergence": [_FMT, _P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
     "ivc_f32_flux_divergence": [_P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
     "ivc_add_host": [_FMT, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P],
+    "ivc_flux_divergence_check": [],
 }
 EXPORTS = sorted(list(_SIGS) + ["ivc_status_string", "ivc_version"])
 
@@ -214,6 +215,12 @@ def flux_divergence(fmt, F, D, ne=None, out=None, stream=None):
                                     _ptr(out), out.shape[2], _stream(stream)),
          "ivc_flux_divergence")
     return out
+
+
+def flux_divergence_check():
+    """Raises IvcError if a flux-divergence launch ended early on a bounded
+    wait since the last check (synchronises the device)."""
+    _chk(load().ivc_flux_divergence_check(), "ivc_flux_divergence_check")
 
 
 def f32_flux_divergence(F, D, ne=None, out=None, stream=None):

@@ -52,6 +52,7 @@ def _run(fname, order, ne, nvars=5, ld=None, h=2 * math.pi / 16):
     Dd = torch.from_numpy(D).to(DEV)
     out = torch.full((ns, nvars, ld), 7.0, dtype=torch.float32, device=DEV)
     ivc.flux_divergence(fg, Wd, Dd, ne=ne, out=out)
+    ivc.flux_divergence_check()   # no bounded wait ran out
     got = out.cpu().numpy()
     ref = O.flux_divergence(fo, w, D, ns, nvars)
     X = O.decompress(fo, w.reshape(-1)).reshape(ns, nvars, ne, 3)
@@ -100,6 +101,7 @@ def test_f32_flux_divergence_baseline():
     D = synth.fr_hex_operator(order, 0.3)
     Fc = np.ascontiguousarray(np.transpose(F, (3, 0, 1, 2)))        # (3, ns, nvars, ne)
     out = ivc.f32_flux_divergence(torch.from_numpy(Fc).to(DEV), torch.from_numpy(D).to(DEV))
+    ivc.flux_divergence_check()
     got = out.cpu().numpy().astype(np.float64)
     Dd = D.astype(np.float64).reshape(3, ns, ns)
     ref = np.einsum("cjk,jpec->kpe", Dd, F.astype(np.float64))
