@@ -380,8 +380,7 @@ ivc_status ivc_compress(const ivc_format *fmt, const float *xyz, ivc_layout layo
   if (n == 0) return IVC_OK;
   if (!xyz || !w) return IVC_ERR_ARG;
   if (!aligned(xyz, 4) || !aligned(w, 8) || (counts && !aligned(counts, 8))) return IVC_ERR_ALIGN;
-  if (layout == IVC_AOS && aligned(xyz, 8) && aligned(w, 16) && map == IVC_MAP_UNIFORM &&
-      fast::is_primary(F)) {
+  if (layout == IVC_AOS && aligned(xyz, 8) && aligned(w, 16) && fast::fast_geometry(map, F) != 0) {
     const LaunchShape s = default_shape(map, K_COMPRESS_FAST, F, n, 1, nullptr);
     return cuda_status(launch_compress_fast(F, xyz, n, w, counts, s, stream));
   }
@@ -400,8 +399,7 @@ ivc_status ivc_decompress(const ivc_format *fmt, const uint64_t *w, int64_t n, f
   if (n == 0) return IVC_OK;
   if (!xyz || !w) return IVC_ERR_ARG;
   if (!aligned(xyz, 4) || !aligned(w, 8)) return IVC_ERR_ALIGN;
-  if (layout == IVC_AOS && aligned(xyz, 8) && aligned(w, 16) && map == IVC_MAP_UNIFORM &&
-      fast::is_primary(F)) {
+  if (layout == IVC_AOS && aligned(xyz, 8) && aligned(w, 16) && fast::fast_geometry(map, F) != 0) {
     const LaunchShape s = default_shape(map, K_DECOMPRESS_FAST, F, n, 1, nullptr);
     return cuda_status(launch_decompress_fast(F, w, n, xyz, s, stream));
   }
@@ -421,7 +419,7 @@ ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t 
   if (!aligned(a, 8) || !aligned(b, 8) || !aligned(c, 8)) return IVC_ERR_ALIGN;
   const int vec2 = (aligned(a, 16) && aligned(b, 16) && aligned(c, 16) &&
                     !(cfg && cfg->vec_per_thread == 1)) ? 1 : 0;
-  if (vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F)) {
+  if (vec2 && fast::fast_geometry(map, F) != 0) {
     const LaunchShape s = default_shape(map, K_ADD_FAST, F, n, 1, cfg);
     return cuda_status(launch_add_fast(F, a, b, c, n, s, stream));
   }
@@ -445,7 +443,7 @@ ivc_status ivc_axpy(const ivc_format *fmt, float alpha, const uint64_t *x, uint6
   if (!x || !y) return IVC_ERR_ARG;
   if (!aligned(x, 8) || !aligned(y, 8)) return IVC_ERR_ALIGN;
   const int vec2 = (aligned(x, 16) && aligned(y, 16)) ? 1 : 0;
-  if (vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F)) {
+  if (vec2 && fast::fast_geometry(map, F) != 0) {
     const LaunchShape s = default_shape(map, K_AXPY_FAST, F, n, 1, nullptr);
     return cuda_status(launch_axpy_fast(F, alpha, x, y, n, s, stream));
   }
@@ -468,7 +466,7 @@ ivc_status ivc_pointwise_update(const ivc_format *fmt, float dt, const uint64_t 
     return IVC_ERR_ALIGN;
   const bool al = aligned(v, 16) && aligned(f, 16) && aligned(v_out, 16) &&
                   (!m_out || aligned(m_out, 16)) && (!rho || aligned(rho, 8));
-  if (al && map == IVC_MAP_UNIFORM && fast::is_primary(F)) {
+  if (al && fast::fast_geometry(map, F) != 0) {
     const LaunchShape s = default_shape(map, K_UPDATE_FAST, F, n, 1, nullptr);
     return cuda_status(launch_update_fast(F, dt, v, f, rho, v_out, m_out, n, s, stream));
   }
@@ -502,7 +500,7 @@ ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t
   if (st != IVC_OK || ne == 0) return st;
   st = make_devformat(fmt, &Fm, &map);
   if (st != IVC_OK) return st;
-  const bool fastp = map == IVC_MAP_UNIFORM && fast::is_primary(Fm);
+  const bool fastp = fast::fast_geometry(map, Fm) == 1;
   return cuda_status(launch_flux_div(map, fastp, false, Fm, F, ld, ns, nvars, ne, D, div, ld_out,
                                      stream));
 }
@@ -604,7 +602,7 @@ ivc_status ivc_plan_batched(const ivc_format *fmt, ivc_op op, const ivc_field *f
     return IVC_ERR_CUDA;
   }
   p->P = PlanDev{d_fields, d_tiles, d_counter, d_status, total_tiles, nfields, tile};
-  const bool fastp = p->map == IVC_MAP_UNIFORM && fast::is_primary(p->F);
+  const bool fastp = fast::fast_geometry(p->map, p->F) != 0;
   const int kind = op == IVC_OP_ADD ? (fastp ? K_BATCH_ADD_FAST : K_BATCH_ADD)
                                     : (fastp ? K_BATCH_AXPY_FAST : K_BATCH_AXPY);
   LaunchShape s;
@@ -692,7 +690,7 @@ ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const u
   }
   float best_ms = 1e30f;
   ivc_launch_config bc{256, vec2 ? 2 : 1, 8192, 0};
-  const bool fast_kind = vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F);
+  const bool fast_kind = vec2 && fast::fast_geometry(map, F) != 0;
   for (int blk : blocks) {
     const int okind = fast_kind ? (op == IVC_OP_ADD ? K_ADD_FAST : K_AXPY_FAST) : kind;
     const size_t smem = kernel_smem_bytes(F, map, okind, blk);
@@ -703,7 +701,7 @@ ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const u
       float ms_min = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, stream);
-        const bool fastp = vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F);
+        const bool fastp = vec2 && fast::fast_geometry(map, F) != 0;
         cudaError_t e;
         if (fastp) {
           const LaunchShape sf =

@@ -1,5 +1,6 @@
 // Fast path for the paper's primary layout <0,7,22>-17-18, b7 = 80 (Sec. 3,
-// Sec. 5), uniform map, default range handling.  Same results as the generic
+// Sec. 5), and for its fractional split at n_phi_max + 1 = floor(2^17.5)
+// (Sec. 2.4), default range handling.  Same results as the generic
 // path in ivc_device.cuh (shared tables, same error bounds, same FP64
 // fallbacks); organised for GB300 issue throughput:
 //   * every thread carries two vectors and does their FP32 arithmetic with the
@@ -7,10 +8,10 @@
 //   * field extraction, the exact angle folds and table addressing use float
 //     arithmetic on exact small integers and magic-number rounding, keeping
 //     the integer/compare pipe for the few decisions that need it;
-//   * encoding estimates t with an octant-reduced atan polynomial (error about
-//     0.01 bin in t) and runs the error-free side-of-boundary test only for
-//     coordinates within 0.03 bin of a rounding boundary, in a warp loop over
-//     the pending tests;
+//   * encoding estimates t with a double-float octant-reduced atan (error
+//     below 0.0035 bin in t) and runs the error-free side-of-boundary test only
+//     for coordinates within kEps of a rounding boundary, deferred to a
+//     per-warp queue;
 //   * vectors outside |x|_inf in [2^-32, 2^32] (zero, NaN, Inf, tiny, huge) and
 //     non-finite words take the generic code, off the common path.
 #pragma once
@@ -19,22 +20,61 @@
 namespace ivc {
 namespace fast {
 
-constexpr int kN = 262143;          // n_theta_max
-constexpr int kM = 131071;          // n_phi_max
-constexpr int kDt = kN;             // theta grid pi m / N
-constexpr int kDp = 2 * kM;         // phi grid pi m / (2M)
-constexpr int kShift = 8;           // table step 2^8 units (both grids)
-constexpr int kNent = 513;          // entries per grid
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
 constexpr float kEps = 0.005f;      // bin-coordinate estimate error bound (with margin)
 
-// The primary layout is the one this path serves.
-__host__ __device__ inline bool is_primary(const DevFormat &F) {
+// The layouts this path serves: grid sizes n_theta_max = N, n_phi_max = M,
+// head-table steps 2^ST (theta grid pi m / N) and 2^SP (phi grid
+// pi m / (2M)) with NT, NP entries, and the packing of the angle codes below
+// the 29 magnitude bits (E7 in bits 57..63, m22 in 35..56).
+struct GeoPrimary {  // <0,7,22>-17-18: n_phi in bits 18..34, n_theta in 0..17
+  static constexpr int N = 262143, M = 131071;
+  static constexpr int ST = 8, SP = 8, NT = 513, NP = 513;
+  static constexpr int MAP = MAP_UNIFORM;
+  __device__ static void unpack(uint32_t hi, uint32_t lo, uint32_t &nt, uint32_t &np) {
+    nt = lo & 0x3FFFFu;
+    np = __funnelshift_r(lo, hi, 18) & 0x1FFFFu;
+  }
+  __device__ static uint64_t pack(uint32_t hi_mag, int np, int nt) {
+    return ((uint64_t)(hi_mag | ((uint32_t)np >> 14)) << 32) |
+           (((uint32_t)np << 18) | (uint32_t)nt);
+  }
+};
+
+// Fractional split (Sec. 2.4) at n_phi_max + 1 = 185363, n_theta_max + 1 =
+// floor(2^35 / 185363) = 185364: n_p = n_phi (N + 1) + n_theta in bits 0..34.
+struct GeoSplit {
+  static constexpr int N = 185363, M = 185362;
+  static constexpr int ST = 7, SP = 8, NT = 725, NP = 725;
+  static constexpr int MAP = MAP_FRACSPLIT;
+  __device__ static void unpack(uint32_t hi, uint32_t lo, uint32_t &nt, uint32_t &np) {
+    const uint64_t npk = ((uint64_t)(hi & 7u) << 32) | lo;
+    const uint64_t q = npk / (uint64_t)(N + 1);
+    nt = (uint32_t)(npk - q * (uint64_t)(N + 1));
+    // codes beyond (M + 1)(N + 1) - 1 are not valid: n_phi clamped as in the
+    // generic decoder
+    np = q > (uint64_t)M ? (uint32_t)M : (uint32_t)q;
+  }
+  __device__ static uint64_t pack(uint32_t hi_mag, int np, int nt) {
+    // n_p < 2^35: its bits 32..34 fill the three free low bits of hi_mag
+    return ((uint64_t)hi_mag << 32) + ((uint64_t)np * (uint64_t)(N + 1) + (uint64_t)nt);
+  }
+};
+
+template <class G>
+__host__ __device__ inline bool is_geo(const DevFormat &F) {
   return F.sh_phi == 18 && F.sh_m == 35 && F.sh_e == 57 && F.mask_e == 127u &&
-         F.mask_m == 0x3FFFFFu && F.e_off == -47 && F.N == kN && F.M == kM && F.st == kShift &&
-         F.sp == kShift && F.nent_t == kNent && F.nent_p == kNent && F.under_mode == 0 &&
-         F.over_mode == 0;
+         F.mask_m == 0x3FFFFFu && F.e_off == -47 && F.N == G::N && F.M == G::M &&
+         F.st == G::ST && F.sp == G::SP && F.nent_t == G::NT && F.nent_p == G::NP &&
+         F.under_mode == 0 && F.over_mode == 0;
+}
+
+// Which fast layout a format is: 1 primary, 2 fractional split, 0 none.
+__host__ __device__ inline int fast_geometry(int map, const DevFormat &F) {
+  if (map == MAP_UNIFORM && is_geo<GeoPrimary>(F)) return 1;
+  if (map == MAP_FRACSPLIT && is_geo<GeoSplit>(F)) return 2;
+  return 0;
 }
 
 __device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
@@ -60,13 +100,15 @@ struct Fold2 {
   bool swap0, swap1, cneg0, cneg1;
 };
 
-// cos/sin magnitudes of pi b / (2D) for both elements from the shared table.
+// cos/sin magnitudes of pi b / (2D) for both elements from the shared table
+// (entries at b = h 2^S).
+template <int S>
 __device__ __forceinline__ void sincos2(float2 b, const TabEntry *__restrict__ tab, float Kh,
                                         float Kl, FF2 &c, FF2 &s) {
-  // h = nearest integer to b / 256 (magic-number rounding), l = b - 256 h
-  const float2 hb = fma2(b, bc(1.0f / 256.0f), bc(kMagic));
+  // h = nearest integer to b / 2^S (magic-number rounding), l = b - 2^S h
+  const float2 hb = fma2(b, bc(1.0f / (float)(1 << S)), bc(kMagic));
   const float2 hf = add2(hb, bc(-kMagic));
-  const float2 lf = fma2(hf, bc(-256.0f), b);
+  const float2 lf = fma2(hf, bc(-(float)(1 << S)), b);
   const uint32_t i0 = __float_as_uint(hb.x) - kMagicBits;
   const uint32_t i1 = __float_as_uint(hb.y) - kMagicBits;
   const TabEntry e0 = tab[i0];
@@ -147,6 +189,7 @@ __device__ __forceinline__ float apply_neg(float v, bool n) { return (n && v != 
 
 // Decodes two words; returns false in *ok for an element that needs the
 // generic path (non-finite word or an ambiguous rounding).
+template <class G>
 __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry *__restrict__ tab_t,
                                         const TabEntry *__restrict__ tab_p, float Kt_h,
                                         float Kt_l, float Kp_h, float Kp_l, float2 &X,
@@ -159,28 +202,29 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry
   const float r1 = E1 == 0u ? 0.0f : __uint_as_float(((hi1 >> 2) & 0xFFFFFFFEu) + (47u << 23));
   slow0 = (E0 == 127u);
   slow1 = (E1 == 127u);
-  // n_theta, n_phi as exact floats (magic-number conversion)
-  const float2 ntf = add2(make_float2(__uint_as_float((lo0 & 0x3FFFFu) | 0x4B000000u),
-                                      __uint_as_float((lo1 & 0x3FFFFu) | 0x4B000000u)),
+  // n_theta, n_phi as exact floats (magic-number conversion, codes < 2^23)
+  uint32_t nt0, np0, nt1, np1;
+  G::unpack(hi0, lo0, nt0, np0);
+  G::unpack(hi1, lo1, nt1, np1);
+  const float2 ntf = add2(make_float2(__uint_as_float(nt0 | 0x4B000000u),
+                                      __uint_as_float(nt1 | 0x4B000000u)),
                           bc(-8388608.0f));
-  const float2 npf = add2(make_float2(__uint_as_float((__funnelshift_r(lo0, hi0, 18) & 0x1FFFFu) |
-                                                      0x4B000000u),
-                                      __uint_as_float((__funnelshift_r(lo1, hi1, 18) & 0x1FFFFu) |
-                                                      0x4B000000u)),
+  const float2 npf = add2(make_float2(__uint_as_float(np0 | 0x4B000000u),
+                                      __uint_as_float(np1 | 0x4B000000u)),
                           bc(-8388608.0f));
   // theta^ = pi (2 n_theta - N) / N
-  const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)kN));
-  const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)kDt);
+  const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)G::N));
+  const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)G::N);
   FF2 cc, ss;
-  sincos2(ft.b, tab_t, Kt_h, Kt_l, cc, ss);
+  sincos2<G::ST>(ft.b, tab_t, Kt_h, Kt_l, cc, ss);
   FF2 ct, st;
   ct.h = sel2(ft.swap0, ft.swap1, ss.h, cc.h);
   ct.l = sel2(ft.swap0, ft.swap1, ss.l, cc.l);
   st.h = sel2(ft.swap0, ft.swap1, cc.h, ss.h);
   st.l = sel2(ft.swap0, ft.swap1, cc.l, ss.l);
   // phi^ = pi (2 n_phi) / (2M)
-  const Fold2 fp = fold2(add2(npf, npf), (float)kDp);
-  sincos2(fp.b, tab_p, Kp_h, Kp_l, cc, ss);
+  const Fold2 fp = fold2(add2(npf, npf), (float)(2 * G::M));
+  sincos2<G::SP>(fp.b, tab_p, Kp_h, Kp_l, cc, ss);
   FF2 cp, sp;
   cp.h = sel2(fp.swap0, fp.swap1, ss.h, cc.h);
   cp.l = sel2(fp.swap0, fp.swap1, ss.l, cc.l);
@@ -286,11 +330,13 @@ __device__ __forceinline__ BinCoord2 bin_coord2(float2 K0, float2 s1, float2 bh,
 }
 
 struct Est2 {
-  float2 fl_t, fr_t;   // theta: t = 131071 + h, h = w + 1/2 (floor of h, frac)
+  float2 fl_t, fr_t;   // theta: t = (N - 1) / 2 + h, h = w + 1/2 (floor of h, frac)
   float2 fl_p, fr_p;   // phi:   t directly
 };
 
+template <class G>
 __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r2h, float2 r2l) {
+  constexpr int kN = G::N, kM = G::M;
   Est2 e;
   // theta = atan2(y, x); t = N/2 + w, h = w + 1/2 = K0 + 1/2 + s1 g,
   // g = N beta / (2 pi), beta = atan(min/max of |x|, |y|)
@@ -351,6 +397,7 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
 // Error-free side test for one pending decision (generic tables and FP64
 // fallback): kind 0 the theta boundary k + 1/2, kind 1 the phi boundary.
 // One straight path for both kinds.
+template <class G>
 __device__ __forceinline__ int exact_side(int kind, int k, float xs, float ys, float zs,
                                           const DevFormat &F, const TabEntry *tab_t,
                                           const TabEntry *tab_p) {
@@ -382,23 +429,21 @@ __device__ __forceinline__ int exact_side(int kind, int k, float xs, float ys, f
   }
   const int side = side_ge(a, a_l, c, ph ? zs : xs, s);
   if (side >= 0) return side;
-  return ph ? side_phi_f64<MAP_UNIFORM>(xs, ys, zs, k, F)
-            : side_theta_f64<MAP_UNIFORM>(xs, ys, k, F);
+  return ph ? side_phi_f64<G::MAP>(xs, ys, zs, k, F)
+            : side_theta_f64<G::MAP>(xs, ys, k, F);
 }
 
+template <int MAP>
 static __device__ __noinline__ uint64_t encode_generic(float x, float y, float z, const DevFormat &F,
                                                        const TabEntry *tab_t,
                                                        const TabEntry *tab_p, uint32_t &flags) {
-  return encode_vec<MAP_UNIFORM>(x, y, z, F, tab_t, tab_p, flags);
+  return encode_vec<MAP>(x, y, z, F, tab_t, tab_p, flags);
 }
 
+template <int MAP>
 static __device__ __noinline__ float3 decode_generic(uint64_t w, const DevFormat &F, const TabEntry *tab_t,
                                               const TabEntry *tab_p) {
-  return decode_word<MAP_UNIFORM>(w, F, tab_t, tab_p);
-}
-
-__device__ __forceinline__ uint64_t pack_word(uint32_t hi, int np, int nt) {
-  return ((uint64_t)(hi | ((uint32_t)np >> 14)) << 32) | (((uint32_t)np << 18) | (uint32_t)nt);
+  return decode_word<MAP>(w, F, tab_t, tab_p);
 }
 
 // Result of encode2 for two vectors: provisional words and what the deferred
@@ -414,9 +459,11 @@ struct Enc2 {
 // Encodes two vectors.  The word of a vector with a pending exact decision
 // is provisional: the caller queues it with push2.  Range events (fl0 / fl1)
 // come only from vectors on the generic path.
+template <class G>
 __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevFormat &F,
                                         const TabEntry *__restrict__ tab_t,
                                         const TabEntry *__restrict__ tab_p) {
+  constexpr int kN = G::N, kM = G::M;
   Enc2 r;
   // |x|_inf in [2^-32, 2^32): no scaling, no range limits, no specials
   // (integer max of the magnitude bits: NaN compares above every finite value)
@@ -454,10 +501,10 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   if (nslow0 && !gen0) r32.x = norm_rn_f64(x.x, y.x, z.x);
   if (nslow1 && !gen1) r32.y = norm_rn_f64(x.y, y.y, z.y);
   // angle estimates
-  const Est2 e = estimate2(x, y, z, r2h, r2l);
+  const Est2 e = estimate2<G>(x, y, z, r2h, r2l);
   // k = floor(t) clamped to [0, n_max - 1]; the fraction absorbs the clamp
   // (t = n_max gives fraction 1, t < 0 a negative one: never flagged)
-  float2 ft = add2(e.fl_t, bc(131071.0f));
+  float2 ft = add2(e.fl_t, bc((float)((kN - 1) / 2)));
   const float2 ftc = make_float2(fminf(fmaxf(ft.x, 0.0f), (float)(kN - 1)),
                                  fminf(fmaxf(ft.y, 0.0f), (float)(kN - 1)));
   const float2 frt = add2(e.fr_t, sub2(ft, ftc));
@@ -484,11 +531,11 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   const uint32_t rb0 = __float_as_uint(r32.x), rb1 = __float_as_uint(r32.y);
   r.hi0 = ((rb0 - (47u << 23)) << 2) & 0xFFFFFFF8u;
   r.hi1 = ((rb1 - (47u << 23)) << 2) & 0xFFFFFFF8u;
-  r.w0 = pack_word(r.hi0, np0, nt0);
-  r.w1 = pack_word(r.hi1, np1, nt1);
+  r.w0 = G::pack(r.hi0, np0, nt0);
+  r.w1 = G::pack(r.hi1, np1, nt1);
   r.fl0 = r.fl1 = 0u;
-  if (gen0) r.w0 = encode_generic(x.x, y.x, z.x, F, tab_t, tab_p, r.fl0);
-  if (gen1) r.w1 = encode_generic(x.y, y.y, z.y, F, tab_t, tab_p, r.fl1);
+  if (gen0) r.w0 = encode_generic<G::MAP>(x.x, y.x, z.x, F, tab_t, tab_p, r.fl0);
+  if (gen1) r.w1 = encode_generic<G::MAP>(x.y, y.y, z.y, F, tab_t, tab_p, r.fl1);
   return r;
 }
 
@@ -506,7 +553,7 @@ struct PendItem {
   float x, y, z;   // the encoded vector
   uint32_t hi;     // high word without the n_phi bits
   int nt;          // theta: k when pending, else the code
-  uint32_t npp;    // phi: k when pending, else the code (bits 0..16); kinds (bits 30..31)
+  uint32_t npp;    // phi: k when pending, else the code (bits 0..29); kinds (bits 30..31)
 };
 
 struct WarpQueue {
@@ -523,25 +570,27 @@ __device__ __forceinline__ WarpQueue warp_queue(void *base) {
 
 // Runs once per 32 queued items: kept out of line so that the main loop's
 // register allocation does not carry the exact test.
+template <class G>
 static __device__ __noinline__ void resolve_item(const PendItem *pit, const DevFormat &F,
                                                  const TabEntry *tab_t, const TabEntry *tab_p) {
   const PendItem it = *pit;
   int nt = it.nt;
-  int np = (int)(it.npp & 0x1FFFFu);
+  int np = (int)(it.npp & 0x3FFFFFFFu);
   const uint32_t pend = it.npp >> 30;
   // one kind-agnostic test per item; a second only when both kinds wait
   const int kind = (pend & 1u) ? 0 : 1;
-  const int side = exact_side(kind, kind ? np : nt, it.x, it.y, it.z, F, tab_t, tab_p);
+  const int side = exact_side<G>(kind, kind ? np : nt, it.x, it.y, it.z, F, tab_t, tab_p);
   if (kind == 0) nt += side;
   else np += side;
-  if (pend == 3u) np += exact_side(1, np, it.x, it.y, it.z, F, tab_t, tab_p);
-  if (nt == kN || np == 0 || np == kM) nt = 0;
-  *it.dst = pack_word(it.hi, np, nt);
+  if (pend == 3u) np += exact_side<G>(1, np, it.x, it.y, it.z, F, tab_t, tab_p);
+  if (nt == G::N || np == 0 || np == G::M) nt = 0;
+  *it.dst = G::pack(it.hi, np, nt);
 }
 
 // Queues the pending vectors of one encode2 result (element 0 -> dst0,
 // element 1 -> dst0 + 1; inactive lanes queue nothing) and resolves full
 // batches.  All lanes of the warp call it.
+template <class G>
 __device__ __forceinline__ void push2(WarpQueue &wq, bool act, const Enc2 &e, float2 x, float2 y,
                                       float2 z, uint64_t *dst0, const DevFormat &F,
                                       const TabEntry *tab_t, const TabEntry *tab_p) {
@@ -560,36 +609,38 @@ __device__ __forceinline__ void push2(WarpQueue &wq, bool act, const Enc2 &e, fl
   wq.count += __popc(b0) + __popc(b1);
   while (wq.count >= 32) {
     __syncwarp();
-    resolve_item(wq.q + wq.count - 32 + (threadIdx.x & 31), F, tab_t, tab_p);
+    resolve_item<G>(wq.q + wq.count - 32 + (threadIdx.x & 31), F, tab_t, tab_p);
     wq.count -= 32;
     __syncwarp();
   }
 }
 
 // Resolves what is left in the queue (all lanes call it).
+template <class G>
 __device__ __forceinline__ void drain(WarpQueue &wq, const DevFormat &F, const TabEntry *tab_t,
                                       const TabEntry *tab_p) {
   if (wq.count == 0) return;
   __syncwarp();
   if ((int)(threadIdx.x & 31) < wq.count) {
-    resolve_item(wq.q + (threadIdx.x & 31), F, tab_t, tab_p);
+    resolve_item<G>(wq.q + (threadIdx.x & 31), F, tab_t, tab_p);
   }
   wq.count = 0;
   __syncwarp();
 }
 
 // Decodes two words through the fast path, falling back per element.
+template <class G>
 __device__ __forceinline__ void decode2_full(uint64_t w0, uint64_t w1, const DevFormat &F,
                                              const TabEntry *tab_t, const TabEntry *tab_p,
                                              float2 &X, float2 &Y, float2 &Z) {
   bool s0, s1;
-  decode2(w0, w1, tab_t, tab_p, F.Kt_h, F.Kt_l, F.Kp_h, F.Kp_l, X, Y, Z, s0, s1);
+  decode2<G>(w0, w1, tab_t, tab_p, F.Kt_h, F.Kt_l, F.Kp_h, F.Kp_l, X, Y, Z, s0, s1);
   if (s0) {
-    const float3 v = decode_generic(w0, F, tab_t, tab_p);
+    const float3 v = decode_generic<G::MAP>(w0, F, tab_t, tab_p);
     X.x = v.x; Y.x = v.y; Z.x = v.z;
   }
   if (s1) {
-    const float3 v = decode_generic(w1, F, tab_t, tab_p);
+    const float3 v = decode_generic<G::MAP>(w1, F, tab_t, tab_p);
     X.y = v.x; Y.y = v.y; Z.y = v.z;
   }
 }

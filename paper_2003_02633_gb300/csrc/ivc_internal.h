@@ -74,7 +74,8 @@ cudaError_t launch_axpy(int map, const DevFormat &F, float alpha, const uint64_t
 cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t *v,
                           const uint64_t *f, const float *rho, uint64_t *v_out, uint64_t *m_out,
                           int64_t n, const LaunchShape &s, cudaStream_t st);
-// Fast path of the primary layout (requires fast::is_primary(F)); two words
+// Fast path of the primary layout and of the default fractional split
+// (requires fast::fast_geometry(map, F) != 0); two words
 // per thread, n >= 0, 16-byte aligned word arrays.
 cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_t *b, uint64_t *c,
                             int64_t n, const LaunchShape &s, cudaStream_t st);

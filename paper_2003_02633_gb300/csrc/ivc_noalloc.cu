@@ -103,7 +103,7 @@ extern "C" ivc_status ivc_add_noalloc(const ivc_format *fmt, const uint64_t *a, 
   }
   const bool vec2 = aligned(a, 16) && aligned(b, 16) && aligned(c, 16);
   cudaError_t e;
-  if (vec2 && map == IVC_MAP_UNIFORM && fast::is_primary(F)) {
+  if (vec2 && fast::fast_geometry(map, F) != 0) {
     e = launch_add_fast(F, a, b, c, n, default_shape(map, K_ADD_FAST, F, n, 1, nullptr), stream);
   } else {
     e = launch_add(map, F, a, b, c, n, default_shape(map, K_ADD, F, n, vec2 ? 1 : 0, nullptr),

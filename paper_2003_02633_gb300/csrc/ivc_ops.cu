@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_update(const __grid_constant__ DevForma
 // calling threads: warp `warp` of `nwarps` takes word pairs warp*32 + lane,
 // (warp + nwarps)*32 + lane, ...; the trip count is uniform per warp.  The odd
 // tail element goes to the thread with warp == 0 and lane == 0.
-template <int OP>
+template <int OP, class G>
 __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64_t *b, uint64_t *c,
                                                  int64_t n, int64_t warp, int64_t nwarps, int lane,
                                                  float alpha, const DevFormat &F,
@@ -239,8 +239,8 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
       nb = __ldcs(b2 + i + nwarps * 32);
     }
     float2 ux, uy, uz, vx, vy, vz;
-    fast::decode2_full(wa.x, wa.y, F, tab_t, tab_p, ux, uy, uz);
-    fast::decode2_full(wb.x, wb.y, F, tab_t, tab_p, vx, vy, vz);
+    fast::decode2_full<G>(wa.x, wa.y, F, tab_t, tab_p, ux, uy, uz);
+    fast::decode2_full<G>(wb.x, wb.y, F, tab_t, tab_p, vx, vy, vz);
     float2 sx, sy, sz;
     if (OP == IVC_OP_ADD) {
       sx = fast::add2(ux, vx); sy = fast::add2(uy, vy); sz = fast::add2(uz, vz);
@@ -249,37 +249,38 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
       sy = fast::fma2(fast::bc(alpha), uy, vy);
       sz = fast::fma2(fast::bc(alpha), uz, vz);
     }
-    const fast::Enc2 e = fast::encode2(sx, sy, sz, F, tab_t, tab_p);
+    const fast::Enc2 e = fast::encode2<G>(sx, sy, sz, F, tab_t, tab_p);
     if (act) __stcs(c2 + i, make_ulonglong2(e.w0, e.w1));
-    fast::push2(wq, act, e, sx, sy, sz, c + 2 * i, F, tab_t, tab_p);
+    fast::push2<G>(wq, act, e, sx, sy, sz, c + 2 * i, F, tab_t, tab_p);
   }
-  fast::drain(wq, F, tab_t, tab_p);
+  fast::drain<G>(wq, F, tab_t, tab_p);
   if ((n & 1) && warp == 0 && lane == 0) {
     uint32_t flags = 0;
     const int64_t i = n - 1;
     if (OP == IVC_OP_ADD)
-      c[i] = fused1<MAP_UNIFORM>(a[i], b[i], OpAdd{}, F, tab_t, tab_p, flags);
+      c[i] = fused1<G::MAP>(a[i], b[i], OpAdd{}, F, tab_t, tab_p, flags);
     else
-      c[i] = fused1<MAP_UNIFORM>(a[i], b[i], OpAxpy{alpha}, F, tab_t, tab_p, flags);
+      c[i] = fused1<G::MAP>(a[i], b[i], OpAxpy{alpha}, F, tab_t, tab_p, flags);
   }
 }
 
-template <int OP>
+template <int OP, class G>
 __global__ void __launch_bounds__(256) k_fused_fast(const __grid_constant__ DevFormat F,
                                                     const uint64_t *a, const uint64_t *b,
                                                     uint64_t *c, int64_t n, float alpha) {
-  IVC_TABLES(F, MAP_UNIFORM);
-  fused_fast_range<OP>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+  IVC_TABLES(F, G::MAP);
+  fused_fast_range<OP, G>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                        ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t,
                        tab_p, IVC_QUEUE(F));
 }
 
 // Compress n AoS vectors (primary layout), two per thread; counts as in
 // k_compress.  Requires a 8-byte aligned xyz and a 16-byte aligned w.
+template <class G>
 __global__ void __launch_bounds__(256, 3) k_compress_fast(const __grid_constant__ DevFormat F,
                                                        const float *__restrict__ xyz, int64_t n,
                                                        uint64_t *w, ivc_counts *counts) {
-  IVC_TABLES(F, MAP_UNIFORM);
+  IVC_TABLES(F, G::MAP);
   const int64_t n2 = n >> 1;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -307,19 +308,19 @@ __global__ void __launch_bounds__(256, 3) k_compress_fast(const __grid_constant_
     }
     const float2 vx = make_float2(p0.x, p1.y), vy = make_float2(p0.y, p2.x),
                  vz = make_float2(p1.x, p2.y);
-    const fast::Enc2 e = fast::encode2(vx, vy, vz, F, tab_t, tab_p);
+    const fast::Enc2 e = fast::encode2<G>(vx, vy, vz, F, tab_t, tab_p);
     if (act) {
       __stcs(w2 + i, make_ulonglong2(e.w0, e.w1));
       ev.add(e.fl0);
       ev.add(e.fl1);
     }
-    fast::push2(wq, act, e, vx, vy, vz, w + 2 * i, F, tab_t, tab_p);
+    fast::push2<G>(wq, act, e, vx, vy, vz, w + 2 * i, F, tab_t, tab_p);
   }
-  fast::drain(wq, F, tab_t, tab_p);
+  fast::drain<G>(wq, F, tab_t, tab_p);
   if ((n & 1) && warp == 0 && lane == 0) {
     const int64_t i = n - 1;
     uint32_t f = 0;
-    w[i] = encode_vec<MAP_UNIFORM>(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], F, tab_t, tab_p, f);
+    w[i] = encode_vec<G::MAP>(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], F, tab_t, tab_p, f);
     ev.add(f);
   }
   flush_counts(ev, counts);
@@ -327,10 +328,11 @@ __global__ void __launch_bounds__(256, 3) k_compress_fast(const __grid_constant_
 
 // Decompress n words (primary layout) to AoS FP32, two per thread.  Requires
 // a 16-byte aligned w and an 8-byte aligned xyz.
+template <class G>
 __global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__ DevFormat F,
                                                          const uint64_t *__restrict__ w,
                                                          int64_t n, float *xyz) {
-  IVC_TABLES(F, MAP_UNIFORM);
+  IVC_TABLES(F, G::MAP);
   const int64_t n2 = n >> 1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(w);
@@ -341,14 +343,14 @@ __global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__
     const ulonglong2 ww = nw;
     if (i + stride < n2) nw = __ldcs(w2 + i + stride);
     float2 X, Y, Z;
-    fast::decode2_full(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z);
+    fast::decode2_full<G>(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z);
     __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
     __stcs(v2 + 3 * i + 1, make_float2(Z.x, X.y));
     __stcs(v2 + 3 * i + 2, make_float2(Y.y, Z.y));
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t i = n - 1;
-    const float3 v = decode_word<MAP_UNIFORM>(w[i], F, tab_t, tab_p);
+    const float3 v = decode_word<G::MAP>(w[i], F, tab_t, tab_p);
     xyz[3 * i] = v.x;
     xyz[3 * i + 1] = v.y;
     xyz[3 * i + 2] = v.z;
@@ -356,11 +358,12 @@ __global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__
 }
 
 // v_out = encode(fmaf(dt, f, v)); m_out = encode(rho * v_new) (if requested).
+template <class G>
 __global__ void __launch_bounds__(256, 3) k_update_fast(const __grid_constant__ DevFormat F, float dt,
                                                      const uint64_t *v, const uint64_t *f,
                                                      const float *__restrict__ rho,
                                                      uint64_t *v_out, uint64_t *m_out, int64_t n) {
-  IVC_TABLES(F, MAP_UNIFORM);
+  IVC_TABLES(F, G::MAP);
   const bool want_m = (rho != nullptr) && (m_out != nullptr);
   const int64_t n2 = n >> 1;
   const int lane = threadIdx.x & 31;
@@ -385,34 +388,34 @@ __global__ void __launch_bounds__(256, 3) k_update_fast(const __grid_constant__ 
       nf = __ldcs(f2 + i + nwarps * 32);
     }
     float2 ux, uy, uz, gx, gy, gz;
-    fast::decode2_full(wv.x, wv.y, F, tab_t, tab_p, ux, uy, uz);
-    fast::decode2_full(wf.x, wf.y, F, tab_t, tab_p, gx, gy, gz);
+    fast::decode2_full<G>(wv.x, wv.y, F, tab_t, tab_p, ux, uy, uz);
+    fast::decode2_full<G>(wf.x, wf.y, F, tab_t, tab_p, gx, gy, gz);
     const float2 sx = fast::fma2(fast::bc(dt), gx, ux);
     const float2 sy = fast::fma2(fast::bc(dt), gy, uy);
     const float2 sz = fast::fma2(fast::bc(dt), gz, uz);
-    const fast::Enc2 e = fast::encode2(sx, sy, sz, F, tab_t, tab_p);
+    const fast::Enc2 e = fast::encode2<G>(sx, sy, sz, F, tab_t, tab_p);
     if (act) __stcs(o2 + i, make_ulonglong2(e.w0, e.w1));
-    fast::push2(wq, act, e, sx, sy, sz, v_out + 2 * i, F, tab_t, tab_p);
+    fast::push2<G>(wq, act, e, sx, sy, sz, v_out + 2 * i, F, tab_t, tab_p);
     if (want_m) {
       const float2 q = act ? make_float2(__ldcs(rho + 2 * i), __ldcs(rho + 2 * i + 1))
                            : make_float2(0.0f, 0.0f);
       const float2 mx = fast::mul2(q, sx), my = fast::mul2(q, sy), mz = fast::mul2(q, sz);
-      const fast::Enc2 em = fast::encode2(mx, my, mz, F, tab_t, tab_p);
+      const fast::Enc2 em = fast::encode2<G>(mx, my, mz, F, tab_t, tab_p);
       if (act) __stcs(m2 + i, make_ulonglong2(em.w0, em.w1));
-      fast::push2(wq, act, em, mx, my, mz, m_out + 2 * i, F, tab_t, tab_p);
+      fast::push2<G>(wq, act, em, mx, my, mz, m_out + 2 * i, F, tab_t, tab_p);
     }
   }
-  fast::drain(wq, F, tab_t, tab_p);
+  fast::drain<G>(wq, F, tab_t, tab_p);
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     uint32_t flags = 0;
     const int64_t i = n - 1;
-    const float3 vv = decode_word<MAP_UNIFORM>(v[i], F, tab_t, tab_p);
-    const float3 ff = decode_word<MAP_UNIFORM>(f[i], F, tab_t, tab_p);
+    const float3 vv = decode_word<G::MAP>(v[i], F, tab_t, tab_p);
+    const float3 ff = decode_word<G::MAP>(f[i], F, tab_t, tab_p);
     const float sx = fmaf(dt, ff.x, vv.x), sy = fmaf(dt, ff.y, vv.y), sz = fmaf(dt, ff.z, vv.z);
-    v_out[i] = encode_vec<MAP_UNIFORM>(sx, sy, sz, F, tab_t, tab_p, flags);
+    v_out[i] = encode_vec<G::MAP>(sx, sy, sz, F, tab_t, tab_p, flags);
     if (want_m) {
       const float q = rho[i];
-      m_out[i] = encode_vec<MAP_UNIFORM>(q * sx, q * sy, q * sz, F, tab_t, tab_p, flags);
+      m_out[i] = encode_vec<G::MAP>(q * sx, q * sy, q * sz, F, tab_t, tab_p, flags);
     }
   }
 }
@@ -464,10 +467,10 @@ __global__ void __launch_bounds__(256) k_batched(const __grid_constant__ DevForm
 
 // Batched persistent kernel on the primary-layout fast path (tiles of an
 // even number of words; 16-byte aligned fields use the packed loop).
-template <int OP>
+template <int OP, class G>
 __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ DevFormat F,
                                                       const __grid_constant__ PlanDev P) {
-  IVC_TABLES(F, MAP_UNIFORM);
+  IVC_TABLES(F, G::MAP);
   __shared__ long long s_tile;
   uint32_t flags = 0;
   bool done = false;
@@ -494,14 +497,14 @@ __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ De
     const bool vec2 = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
                         reinterpret_cast<uintptr_t>(c)) & 15u) == 0;
     if (vec2) {
-      fused_fast_range<OP>(a, b, c, len, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31,
+      fused_fast_range<OP, G>(a, b, c, len, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31,
                            fd.alpha, F, tab_t, tab_p, IVC_QUEUE(F));
     } else if (OP == IVC_OP_ADD) {
-      fused_range<MAP_UNIFORM>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAdd{}, F, tab_t,
-                               tab_p, flags);
+      fused_range<G::MAP>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAdd{}, F, tab_t,
+                          tab_p, flags);
     } else {
-      fused_range<MAP_UNIFORM>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAxpy{fd.alpha}, F,
-                               tab_t, tab_p, flags);
+      fused_range<G::MAP>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAxpy{fd.alpha}, F,
+                          tab_t, tab_p, flags);
     }
   }
   if (!done && threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_TIMEOUT);
@@ -572,11 +575,19 @@ cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t 
 
 cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P,
                            const LaunchShape &s, cudaStream_t st) {
-  if (map == MAP_UNIFORM && fast::is_primary(F)) {
-    if (op == IVC_OP_ADD)
-      k_batched_fast<IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, P);
-    else
-      k_batched_fast<IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, P);
+  const int geo = fast::fast_geometry(map, F);
+  if (geo != 0) {
+    if (op == IVC_OP_ADD) {
+      if (geo == 2)
+        k_batched_fast<IVC_OP_ADD, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, P);
+      else
+        k_batched_fast<IVC_OP_ADD, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, P);
+    } else {
+      if (geo == 2)
+        k_batched_fast<IVC_OP_AXPY, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, P);
+      else
+        k_batched_fast<IVC_OP_AXPY, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, P);
+    }
     return cudaGetLastError();
   }
   if (op == IVC_OP_ADD) {
@@ -595,35 +606,57 @@ cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P
   return cudaGetLastError();
 }
 
+// Fast launchers: the layout (primary or fractional split) is read from F;
+// the caller has checked fast::fast_geometry().
+#define IVC_FAST_GEO(F, CALL_PRIMARY, CALL_SPLIT) \
+  if (fast::is_geo<fast::GeoSplit>(F)) {         \
+    CALL_SPLIT;                                  \
+  } else {                                       \
+    CALL_PRIMARY;                                \
+  }                                              \
+  return cudaGetLastError()
+
 cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_t *b, uint64_t *c,
                             int64_t n, const LaunchShape &s, cudaStream_t st) {
-  k_fused_fast<IVC_OP_ADD><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n, 0.0f);
-  return cudaGetLastError();
+  IVC_FAST_GEO(
+      F,
+      (k_fused_fast<IVC_OP_ADD, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n,
+                                                                                 0.0f)),
+      (k_fused_fast<IVC_OP_ADD, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n,
+                                                                               0.0f)));
 }
 
 cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
                              int64_t n, const LaunchShape &s, cudaStream_t st) {
-  k_fused_fast<IVC_OP_AXPY><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n, alpha);
-  return cudaGetLastError();
+  IVC_FAST_GEO(
+      F,
+      (k_fused_fast<IVC_OP_AXPY, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n,
+                                                                                  alpha)),
+      (k_fused_fast<IVC_OP_AXPY, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n,
+                                                                                alpha)));
 }
 
 cudaError_t launch_compress_fast(const DevFormat &F, const float *xyz, int64_t n, uint64_t *w,
                                  ivc_counts *counts, const LaunchShape &s, cudaStream_t st) {
-  k_compress_fast<<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts);
-  return cudaGetLastError();
+  IVC_FAST_GEO(
+      F, (k_compress_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts)),
+      (k_compress_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts)));
 }
 
 cudaError_t launch_decompress_fast(const DevFormat &F, const uint64_t *w, int64_t n, float *xyz,
                                    const LaunchShape &s, cudaStream_t st) {
-  k_decompress_fast<<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz);
-  return cudaGetLastError();
+  IVC_FAST_GEO(F, (k_decompress_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz)),
+               (k_decompress_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz)));
 }
 
 cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, const uint64_t *f,
                                const float *rho, uint64_t *v_out, uint64_t *m_out, int64_t n,
                                const LaunchShape &s, cudaStream_t st) {
-  k_update_fast<<<s.grid, s.block, s.smem, st>>>(F, dt, v, f, rho, v_out, m_out, n);
-  return cudaGetLastError();
+  IVC_FAST_GEO(F,
+               (k_update_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(
+                   F, dt, v, f, rho, v_out, m_out, n)),
+               (k_update_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(
+                   F, dt, v, f, rho, v_out, m_out, n)));
 }
 
 cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,
@@ -641,13 +674,13 @@ static const void *kernel_ptr(int kind) {
     case K_AXPY: return (const void *)k_axpy<MAP>;
     case K_UPDATE: return (const void *)k_update<MAP>;
     case K_BATCH_ADD: return (const void *)k_batched<MAP, IVC_OP_ADD>;
-    case K_ADD_FAST: return (const void *)k_fused_fast<IVC_OP_ADD>;
-    case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY>;
-    case K_UPDATE_FAST: return (const void *)k_update_fast;
-    case K_BATCH_ADD_FAST: return (const void *)k_batched_fast<IVC_OP_ADD>;
-    case K_COMPRESS_FAST: return (const void *)k_compress_fast;
-    case K_DECOMPRESS_FAST: return (const void *)k_decompress_fast;
-    case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY>;
+    case K_ADD_FAST: return (const void *)k_fused_fast<IVC_OP_ADD, fast::GeoPrimary>;
+    case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY, fast::GeoPrimary>;
+    case K_UPDATE_FAST: return (const void *)k_update_fast<fast::GeoPrimary>;
+    case K_BATCH_ADD_FAST: return (const void *)k_batched_fast<IVC_OP_ADD, fast::GeoPrimary>;
+    case K_COMPRESS_FAST: return (const void *)k_compress_fast<fast::GeoPrimary>;
+    case K_DECOMPRESS_FAST: return (const void *)k_decompress_fast<fast::GeoPrimary>;
+    case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY, fast::GeoPrimary>;
     default: return (const void *)k_batched<MAP, IVC_OP_AXPY>;
   }
 }
