@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(Wb + q * 4);
           if (MODE == FD_FAST) {
-            fast::decode2_full(w.x, w.y, F, tab_t, tab_p, vx, vy, vz);
+            fast::decode2_full<fast::GeoPrimary>(w.x, w.y, F, tab_t, tab_p, vx, vy, vz);
           } else {
             const float3 a = decode_word<MAP>(w.x, F, tab_t, tab_p);
             const float3 c3 = decode_word<MAP>(w.y, F, tab_t, tab_p);
@@ -244,13 +244,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t g = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * kTE;
-    float acc[4][kMaxNv][4];
+    // accumulators in element pairs: packed f32x2 FMAs (same rounding as fmaf)
+    float2 acc[4][kMaxNv][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int p = 0; p < kMaxNv; ++p)
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb) acc[a][p][bb] = 0.0f;
+      for (int p = 0; p < kMaxNv; ++p) acc[a][p][0] = acc[a][p][1] = make_float2(0.0f, 0.0f);
     for (int ch = 0; ch < nchunk; ++ch, ++g) {
       const int b = g & 1;
       const uint32_t u = g >> 1;
@@ -264,23 +263,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int jn = min(kJC, ns - j0);
       const float *X = Xs + b * kXBuf;
       if (kact) {
-        for (int jj = 0; jj < jn; ++jj) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float4 d =
-                *reinterpret_cast<const float4 *>(Ds + (c * ns + j0 + jj) * nsp + 4 * kg);
-            const float dk[4] = {d.x, d.y, d.z, d.w};
+        for (int jj = 0; jj < kJC; ++jj) {
+          if (jj < jn) {
 #pragma unroll
-            for (int p = 0; p < kMaxNv; ++p) {
-              if (p < nv) {
-                const float4 x = *reinterpret_cast<const float4 *>(
-                    X + ((jj * kMaxNv + p) * 3 + c) * kTE + 4 * eg);
-                const float xe[4] = {x.x, x.y, x.z, x.w};
+            for (int c = 0; c < 3; ++c) {
+              const float4 d =
+                  *reinterpret_cast<const float4 *>(Ds + (c * ns + j0 + jj) * nsp + 4 * kg);
+              const float2 dk[4] = {fast::bc(d.x), fast::bc(d.y), fast::bc(d.z), fast::bc(d.w)};
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+              for (int p = 0; p < kMaxNv; ++p) {
+                if (p < nv) {
+                  const float4 x = *reinterpret_cast<const float4 *>(
+                      X + ((jj * kMaxNv + p) * 3 + c) * kTE + 4 * eg);
+                  const float2 x01 = make_float2(x.x, x.y), x23 = make_float2(x.z, x.w);
 #pragma unroll
-                  for (int bb = 0; bb < 4; ++bb)
-                    acc[a][p][bb] = fmaf(dk[a], xe[bb], acc[a][p][bb]);
+                  for (int a = 0; a < 4; ++a) {
+                    acc[a][p][0] = fast::fma2(dk[a], x01, acc[a][p][0]);
+                    acc[a][p][1] = fast::fma2(dk[a], x23, acc[a][p][1]);
+                  }
+                }
               }
             }
           }
@@ -299,13 +301,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (p >= nv) continue;
           float *o = div + ((int64_t)k * nv + p) * ld_out + e0 + 4 * eg;
           const int64_t e = e0 + 4 * eg;
+          const float v[4] = {acc[a][p][0].x, acc[a][p][0].y, acc[a][p][1].x, acc[a][p][1].y};
           if (e + 3 < ne && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
-            __stcs(reinterpret_cast<float4 *>(o),
-                   make_float4(acc[a][p][0], acc[a][p][1], acc[a][p][2], acc[a][p][3]));
+            __stcs(reinterpret_cast<float4 *>(o), make_float4(v[0], v[1], v[2], v[3]));
           } else {
 #pragma unroll
             for (int bb = 0; bb < 4; ++bb)
-              if (e + bb < ne) o[bb] = acc[a][p][bb];
+              if (e + bb < ne) o[bb] = v[bb];
           }
         }
       }
