@@ -45,7 +45,7 @@ def parse_args():
     p.add_argument("--log2n", type=int, default=28)
     p.add_argument("--no-extra", action="store_true", help="skip the baseline/extra measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--workload", choices=["add", "tgv", "batched", "precision", "fdiv"],
+    p.add_argument("--workload", choices=["add", "tgv", "batched", "precision", "fdiv", "sweep"],
                    default="add",
                    help="add: the headline line; the others print their own JSON line")
     p.add_argument("--tgv-elements", type=int, default=96)
@@ -714,6 +714,55 @@ def run_fdiv(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """The paper's size sweep of Sec. 5 (Fig. speedup): compressed add against
+    the FP32x3 add (AoS) for N = 2^10 ... 2^28 on one GPU.  The L2 is flushed
+    (a 512 MB write) before every timed launch, so every size reads its inputs
+    from HBM; the smallest sizes measure launch latency."""
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+    dev = torch.device("cuda", 0)
+    fmt = ivc.default_format()
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    nmax = 1 << 28
+    a = synth.device_vectors(nmax, 21, dev)
+    b = synth.device_vectors(nmax, 22, dev)
+    wa, wb = ivc.compress(fmt, a), ivc.compress(fmt, b)
+    wc, c32 = torch.empty_like(wa), torch.empty_like(a)
+    flush = torch.empty(1 << 27, dtype=torch.float32, device=dev)
+    rows = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ts.sort()
+        return ts[len(ts) // 2]
+
+    for k in range(10, 29, 2):
+        n = 1 << k
+        for _ in range(3):
+            ivc.add(fmt, wa[:n], wb[:n], out=wc[:n], stream=s)
+            ivc.f32_add(a[:n], b[:n], out=c32[:n], stream=s)
+        reps = 20 if k < 26 else 10
+        tc = timed(lambda: ivc.add(fmt, wa[:n], wb[:n], out=wc[:n], stream=s), reps)
+        tf = timed(lambda: ivc.f32_add(a[:n], b[:n], out=c32[:n], stream=s), reps)
+        rows.append({"log2n": k, "compressed_ms": round(tc, 5), "fp32_ms": round(tf, 5),
+                     "compressed_gvec_s": _gvec(n, tc), "fp32_gvec_s": _gvec(n, tf),
+                     "speedup": round(tf / tc, 4)})
+    print(json.dumps({"workload": "size_sweep_add", "format": "<0,7,22>-17-18",
+                      "l2_flush_bytes": 1 << 29, "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -726,6 +775,8 @@ def main():
         run_precision(args)
     elif args.workload == "fdiv":
         run_fdiv(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ivc(args)
 

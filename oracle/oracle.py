@@ -11,8 +11,9 @@ Every function takes NumPy arrays on the host:
   * vectors are float32 arrays of shape (n, 3) (array-of-structures),
   * packed words are uint64 arrays of shape (n,).
 
-Parity status of each function is recorded in the module docstring of the
-pin tests (``tests/test_oracle_pins.py``); every function here is pinned.
+Parity status of each function is recorded in the module docstrings of the
+pin tests (``tests/test_oracle_pins.py``; ``tests/test_oracle_fdiv.py`` for the
+flux divergence of Algorithm 1); every function here is pinned.
 """
 from __future__ import annotations
 
