@@ -45,7 +45,8 @@ def parse_args():
     p.add_argument("--log2n", type=int, default=28)
     p.add_argument("--no-extra", action="store_true", help="skip the baseline/extra measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--workload", choices=["add", "tgv", "batched", "precision", "fdiv", "sweep"],
+    p.add_argument("--workload", choices=["add", "tgv", "batched", "precision", "fdiv", "sweep",
+                                          "gather"],
                    default="add",
                    help="add: the headline line; the others print their own JSON line")
     p.add_argument("--tgv-elements", type=int, default=96)
@@ -763,6 +764,45 @@ def run_sweep(args):
                       "l2_flush_bytes": 1 << 29, "rows": rows}), flush=True)
 
 
+def run_gather(args):
+    """Random access (the unstructured access of Sec. 1): decompress the words at
+    2^28 uniformly random indices into a table of 2^28 vectors, against the
+    FP32 gather from an AoS and from an SoA table of the same vectors."""
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+    dev = torch.device("cuda", 0)
+    fmt = ivc.default_format()
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    n = 1 << args.log2n
+    x = synth.device_vectors(n, 31, dev)
+    w = ivc.compress(fmt, x)
+    g = torch.Generator(device=dev)
+    g.manual_seed(32)
+    idx = torch.randint(0, n, (n,), generator=g, device=dev, dtype=torch.int64)
+    soa = x.t().contiguous()
+    out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    steps, warmup = max(3, min(args.steps, 20)), max(3, min(args.warmup, 5))
+    res = {}
+    for name, fn in (("compressed", lambda: ivc.gather_decompress(fmt, w, idx, out=out, stream=s)),
+                     ("fp32_aos", lambda: ivc.f32_gather(x, idx, out=out, stream=s)),
+                     ("fp32_soa", lambda: ivc.f32_gather(soa, idx, out=out, layout=ivc.IVC_SOA,
+                                                          ld=n, nsrc=n, stream=s))):
+        ms, _ = time_launches(fn, steps, warmup, stream)
+        res[name] = {"ms": round(ms / steps, 4), "gvec_s": _gvec(n, ms / steps)}
+    # bytes moved per vector at 32-byte sector granularity for the random reads
+    line = {"workload": "gather_decompress", "n": n, "table": n, "index": "uniform random int64",
+            "results": res,
+            "speedup_vs_fp32_aos": round(res["fp32_aos"]["ms"] / res["compressed"]["ms"], 4),
+            "speedup_vs_fp32_soa": round(res["fp32_soa"]["ms"] / res["compressed"]["ms"], 4),
+            "sector_bytes_per_vector": {"compressed": 8 + 32 + 12, "fp32_aos": 8 + 44 + 12,
+                                        "fp32_soa": 8 + 96 + 12},
+            "note": "random reads cost whole 32-byte sectors: 32 B for an 8-byte word, 32 or "
+                    "64 B (mean 44) for a 12-byte AoS vector, 3 x 32 B for SoA"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -777,6 +817,8 @@ def main():
         run_fdiv(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "gather":
+        run_gather(args)
     else:
         run_ivc(args)
 

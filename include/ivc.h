@@ -226,6 +226,25 @@ ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t 
                        uint64_t *c, int64_t n, const ivc_launch_config *cfg,
                        ivc_stream_t stream);
 
+/* Random-access decompression (the unstructured access the method is meant
+ * for, Sec. 1): xyz[3i .. 3i+2] = decompress(w[idx[i]]) for 0 <= i < n, with
+ * the decode of Sec. 2.1 / Eq. a_inv (results as ivc_decompress).
+ *   w    device words, nw of them (8-byte aligned; may be NULL when nw == 0).
+ *   idx  device int64 indices (8-byte aligned; 16-byte aligned with an
+ *        8-byte aligned xyz selects the two-per-thread kernel).
+ *   xyz  device FP32 output, AoS, 3 n floats.
+ * An index outside [0, nw) reads nothing and gives NaN components.
+ * Errors: IVC_ERR_ARG (n < 0, nw < 0, NULL pointers), IVC_ERR_ALIGN. */
+ivc_status ivc_gather_decompress(const ivc_format *fmt, const uint64_t *w, int64_t nw,
+                                 const int64_t *idx, int64_t n, float *xyz,
+                                 ivc_stream_t stream);
+
+/* The FP32 baseline of ivc_gather_decompress: out[3i .. 3i+2] = the vector
+ * src[idx[i]] of an AoS source (3 floats per vector) or an SoA source (rows x,
+ * y, z at stride ld >= nsrc).  Out-of-range indices give NaN components. */
+ivc_status ivc_f32_gather(ivc_layout layout, const float *src, int64_t ld, int64_t nsrc,
+                          const int64_t *idx, int64_t n, float *out, ivc_stream_t stream);
+
 /* Divergence of a compressed flux: Algorithm 1 (Sec. 4; Table fr_nse, step
  * 10) of the flux-reconstruction right-hand side.  For every element e and
  * solution point k, and every equation p:

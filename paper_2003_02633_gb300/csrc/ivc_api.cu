@@ -474,6 +474,28 @@ ivc_status ivc_pointwise_update(const ivc_format *fmt, float dt, const uint64_t 
   return cuda_status(launch_update(map, F, dt, v, f, rho, v_out, m_out, n, s, stream));
 }
 
+// ------------------------------------------------------------------ gather
+
+ivc_status ivc_gather_decompress(const ivc_format *fmt, const uint64_t *w, int64_t nw,
+                                 const int64_t *idx, int64_t n, float *xyz,
+                                 ivc_stream_t stream) {
+  if (n < 0 || nw < 0) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = ivc::format_fields(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!idx || !xyz || (nw > 0 && !w)) return IVC_ERR_ARG;
+  if ((w && !aligned(w, 8)) || !aligned(idx, 8) || !aligned(xyz, 4)) return IVC_ERR_ALIGN;
+  st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  const bool fastp = aligned(idx, 16) && aligned(xyz, 8) && fast::fast_geometry(map, F) != 0;
+  LaunchShape s = default_shape(map, fastp ? K_GATHER_FAST : K_GATHER, F, n, fastp ? 1 : 0,
+                                nullptr);
+  s.vec2 = fastp ? 1 : 0;
+  return cuda_status(launch_gather(map, F, w, nw, idx, n, xyz, s, stream));
+}
+
 // ---------------------------------------------------------- flux divergence
 
 namespace {

@@ -93,6 +93,34 @@ ivc_status f32_op(bool axpy, ivc_layout layout, float alpha, const float *a, con
   return st_of(cudaGetLastError());
 }
 
+// FP32 gather (baseline of the gather-decompress): out[i] = src[idx[i]], AoS
+// output; source AoS (3 floats at 3 j) or SoA (rows at stride ld).  Indices
+// outside [0, nsrc) give NaN components without a read.
+template <bool SOA>
+__global__ void __launch_bounds__(256) k_f32_gather(const float *__restrict__ src, int64_t ld,
+                                                    int64_t nsrc, const int64_t *__restrict__ idx,
+                                                    int64_t n, float *out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t j = __ldcs(idx + i);
+    float x = __int_as_float(0x7fc00000), y = x, z = x;
+    if ((uint64_t)j < (uint64_t)nsrc) {
+      if (SOA) {
+        x = __ldg(src + j);
+        y = __ldg(src + ld + j);
+        z = __ldg(src + 2 * ld + j);
+      } else {
+        x = __ldg(src + 3 * j);
+        y = __ldg(src + 3 * j + 1);
+        z = __ldg(src + 3 * j + 2);
+      }
+    }
+    __stcs(out + 3 * i, x);
+    __stcs(out + 3 * i + 1, y);
+    __stcs(out + 3 * i + 2, z);
+  }
+}
+
 // ------------------------------------------------------------ FP16 / BF16
 
 template <int KIND>
@@ -257,6 +285,21 @@ ivc_status ivc_f32_add(ivc_layout layout, const float *a, const float *b, float 
 ivc_status ivc_f32_axpy(ivc_layout layout, float alpha, const float *x, float *y, int64_t ld,
                         int64_t n, ivc_stream_t stream) {
   return f32_op(true, layout, alpha, x, y, y, ld, n, stream);
+}
+
+ivc_status ivc_f32_gather(ivc_layout layout, const float *src, int64_t ld, int64_t nsrc,
+                          const int64_t *idx, int64_t n, float *out, ivc_stream_t stream) {
+  if (n < 0 || nsrc < 0 || (layout != IVC_AOS && layout != IVC_SOA)) return IVC_ERR_ARG;
+  if (layout == IVC_SOA && ld < nsrc) return IVC_ERR_ARG;
+  if (n == 0) return IVC_OK;
+  if (!idx || !out || (nsrc > 0 && !src)) return IVC_ERR_ARG;
+  if ((src && !aligned(src, 4)) || !aligned(idx, 8) || !aligned(out, 4)) return IVC_ERR_ALIGN;
+  const int grid = grid_for(n, 256, 8);
+  if (layout == IVC_SOA)
+    k_f32_gather<true><<<grid, 256, 0, stream>>>(src, ld, nsrc, idx, n, out);
+  else
+    k_f32_gather<false><<<grid, 256, 0, stream>>>(src, ld, nsrc, idx, n, out);
+  return st_of(cudaGetLastError());
 }
 
 ivc_status ivc_half_add(ivc_half_kind kind, const uint16_t *a, const uint16_t *b, uint16_t *c,

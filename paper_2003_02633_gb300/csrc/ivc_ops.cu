@@ -510,6 +510,66 @@ __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ De
   if (!done && threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_TIMEOUT);
 }
 
+// Gather-decompress (random access, the motivation of Sec. 1): xyz[i] =
+// decompress(w[idx[i]]) for i < n, AoS output.  Indices outside [0, nw) read
+// nothing and give NaN components.  Generic kernel: one index per thread.
+template <int MAP>
+__global__ void __launch_bounds__(256) k_gather(const __grid_constant__ DevFormat F,
+                                                const uint64_t *__restrict__ w, int64_t nw,
+                                                const int64_t *__restrict__ idx, int64_t n,
+                                                float *xyz) {
+  IVC_TABLES(F, MAP);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t j = __ldcs(idx + i);
+    float3 v = make_float3(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                           __int_as_float(0x7fc00000));
+    if ((uint64_t)j < (uint64_t)nw) v = decode_word<MAP>(__ldg(w + j), F, tab_t, tab_p);
+    __stcs(xyz + 3 * i, v.x);
+    __stcs(xyz + 3 * i + 1, v.y);
+    __stcs(xyz + 3 * i + 2, v.z);
+  }
+}
+
+// Fast-path gather: two indices per thread (16-byte index loads), packed
+// decode, the same AoS stores as k_decompress_fast.  Requires a 16-byte aligned
+// idx and an 8-byte aligned xyz.
+template <class G>
+__global__ void __launch_bounds__(256) k_gather_fast(const __grid_constant__ DevFormat F,
+                                                     const uint64_t *__restrict__ w, int64_t nw,
+                                                     const int64_t *__restrict__ idx, int64_t n,
+                                                     float *xyz) {
+  IVC_TABLES(F, G::MAP);
+  const int64_t n2 = n >> 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const longlong2 *i2 = reinterpret_cast<const longlong2 *>(idx);
+  float2 *v2 = reinterpret_cast<float2 *>(xyz);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const longlong2 jj = __ldcs(i2 + i);
+    const bool ok0 = (uint64_t)jj.x < (uint64_t)nw, ok1 = (uint64_t)jj.y < (uint64_t)nw;
+    const uint64_t w0 = ok0 ? __ldg(w + jj.x) : 0ull;
+    const uint64_t w1 = ok1 ? __ldg(w + jj.y) : 0ull;
+    float2 X, Y, Z;
+    fast::decode2_full<G>(w0, w1, F, tab_t, tab_p, X, Y, Z);
+    const float qn = __int_as_float(0x7fc00000);
+    if (!ok0) X.x = Y.x = Z.x = qn;
+    if (!ok1) X.y = Y.y = Z.y = qn;
+    __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
+    __stcs(v2 + 3 * i + 1, make_float2(Z.x, X.y));
+    __stcs(v2 + 3 * i + 2, make_float2(Y.y, Z.y));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
+    const int64_t j = idx[i];
+    float3 v = make_float3(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                           __int_as_float(0x7fc00000));
+    if ((uint64_t)j < (uint64_t)nw) v = decode_word<G::MAP>(w[j], F, tab_t, tab_p);
+    xyz[3 * i] = v.x;
+    xyz[3 * i + 1] = v.y;
+    xyz[3 * i + 2] = v.z;
+  }
+}
+
 // Tiles per field and their prefix sums (one block; nfields is small).
 __global__ void k_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -659,6 +719,19 @@ cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, 
                    F, dt, v, f, rho, v_out, m_out, n)));
 }
 
+cudaError_t launch_gather(int map, const DevFormat &F, const uint64_t *w, int64_t nw,
+                          const int64_t *idx, int64_t n, float *xyz, const LaunchShape &s,
+                          cudaStream_t st) {
+  if (s.vec2 && fast::fast_geometry(map, F) != 0) {
+    IVC_FAST_GEO(F,
+                 (k_gather_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, w, nw, idx,
+                                                                                   n, xyz)),
+                 (k_gather_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, w, nw, idx, n,
+                                                                                 xyz)));
+  }
+  IVC_DISPATCH_MAP(map, k_gather, F, w, nw, idx, n, xyz);
+}
+
 cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,
                              cudaStream_t st) {
   k_tile_scan<<<1, 32, 0, st>>>(fields, nfields, tile, tile_start);
@@ -681,6 +754,8 @@ static const void *kernel_ptr(int kind) {
     case K_COMPRESS_FAST: return (const void *)k_compress_fast<fast::GeoPrimary>;
     case K_DECOMPRESS_FAST: return (const void *)k_decompress_fast<fast::GeoPrimary>;
     case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY, fast::GeoPrimary>;
+    case K_GATHER: return (const void *)k_gather<MAP>;
+    case K_GATHER_FAST: return (const void *)k_gather_fast<fast::GeoPrimary>;
     default: return (const void *)k_batched<MAP, IVC_OP_AXPY>;
   }
 }

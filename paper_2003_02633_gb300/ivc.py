@@ -88,6 +88,8 @@ _SIGS = {
     "ivc_f32_flux_divergence": [_P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
     "ivc_add_host": [_FMT, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P],
     "ivc_flux_divergence_check": [],
+    "ivc_gather_decompress": [_FMT, _P, _I64, _P, _I64, _P, _P],
+    "ivc_f32_gather": [_I, _P, _I64, _I64, _P, _I64, _P, _P],
 }
 EXPORTS = sorted(list(_SIGS) + ["ivc_status_string", "ivc_version"])
 
@@ -249,6 +251,30 @@ def add_host(fmt, a, b, out, workspace, stream=None):
                              a.shape[0], _ptr(workspace),
                              workspace.numel() * workspace.element_size(), _stream(stream)),
          "ivc_add_host")
+    return out
+
+
+def gather_decompress(fmt, w, idx, out=None, stream=None):
+    """xyz[i] = decompress(w[idx[i]]): w (nw,) int64 words, idx (n,) int64 CUDA
+    tensors; returns (n, 3) float32 (NaN rows for out-of-range indices)."""
+    import torch
+    n = idx.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=idx.device)
+    _chk(load().ivc_gather_decompress(ctypes.byref(fmt), _ptr(w), w.shape[0], _ptr(idx), n,
+                                      _ptr(out), _stream(stream)), "ivc_gather_decompress")
+    return out
+
+
+def f32_gather(src, idx, out=None, layout=IVC_AOS, ld=0, nsrc=None, stream=None):
+    """out[i] = src vector idx[i]: AoS src (nsrc, 3) or SoA rows at stride ld."""
+    import torch
+    n = idx.shape[0]
+    nsrc = (src.shape[0] if layout == IVC_AOS else ld) if nsrc is None else nsrc
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=idx.device)
+    _chk(load().ivc_f32_gather(layout, _ptr(src), ld, nsrc, _ptr(idx), n, _ptr(out),
+                               _stream(stream)), "ivc_f32_gather")
     return out
 
 

@@ -87,6 +87,16 @@ def test_argument_errors_before_device_work(lib):
     assert fd(ctypes.byref(f), None, 0, 64, 5, 2, None, None, 2, None) == ivc.IVC_ERR_ARG
     assert fd(ctypes.byref(f), None, 0, 64, 5, 0, None, None, 0, None) == ivc.IVC_OK
     assert fd(ctypes.byref(bad), None, 0, 64, 5, 0, None, None, 0, None) == ivc.IVC_ERR_FORMAT
+    gd = lib.ivc_gather_decompress
+    assert gd(ctypes.byref(f), None, 0, None, -1, None, None) == ivc.IVC_ERR_ARG
+    assert gd(ctypes.byref(f), None, -1, None, 1, None, None) == ivc.IVC_ERR_ARG
+    assert gd(ctypes.byref(f), None, 0, None, 0, None, None) == ivc.IVC_OK
+    assert gd(ctypes.byref(f), None, 4, None, 1, None, None) == ivc.IVC_ERR_ARG
+    assert gd(ctypes.byref(bad), None, 0, None, 1, None, None) == ivc.IVC_ERR_FORMAT
+    fg = lib.ivc_f32_gather
+    assert fg(0, None, 0, 0, None, -1, None, None) == ivc.IVC_ERR_ARG
+    assert fg(1, None, 2, 4, None, 1, None, None) == ivc.IVC_ERR_ARG   # SoA ld < nsrc
+    assert fg(0, None, 0, 0, None, 0, None, None) == ivc.IVC_OK
     ah = lib.ivc_add_host
     assert ah(ctypes.byref(f), None, None, None, -1, None, 0, None) == ivc.IVC_ERR_ARG
     assert ah(ctypes.byref(f), None, None, None, 0, None, 0, None) == ivc.IVC_OK
