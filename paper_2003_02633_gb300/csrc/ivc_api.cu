@@ -489,11 +489,8 @@ ivc_status ivc_gather_decompress(const ivc_format *fmt, const uint64_t *w, int64
   if ((w && !aligned(w, 8)) || !aligned(idx, 8) || !aligned(xyz, 4)) return IVC_ERR_ALIGN;
   st = make_devformat(fmt, &F, &map);
   if (st != IVC_OK) return st;
-  const bool fastp = aligned(idx, 16) && aligned(xyz, 8) && fast::fast_geometry(map, F) != 0;
-  LaunchShape s = default_shape(map, fastp ? K_GATHER_FAST : K_GATHER, F, n, fastp ? 1 : 0,
-                                nullptr);
-  s.vec2 = fastp ? 1 : 0;
-  return cuda_status(launch_gather(map, F, w, nw, idx, n, xyz, s, stream));
+  const bool pairs = aligned(idx, 16) && aligned(xyz, 8);
+  return cuda_status(launch_gather(map, F, w, nw, idx, n, xyz, pairs, stream));
 }
 
 // ---------------------------------------------------------- flux divergence

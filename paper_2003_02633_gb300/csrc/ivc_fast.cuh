@@ -26,12 +26,21 @@ constexpr float kEps = 0.005f;      // bin-coordinate estimate error bound (with
 
 // The layouts this path serves: grid sizes n_theta_max = N, n_phi_max = M,
 // head-table steps 2^ST (theta grid pi m / N) and 2^SP (phi grid
-// pi m / (2M)) with NT, NP entries, and the packing of the angle codes below
-// the 29 magnitude bits (E7 in bits 57..63, m22 in 35..56).
-struct GeoPrimary {  // <0,7,22>-17-18: n_phi in bits 18..34, n_theta in 0..17
+// pi m / (2M)) with NT, NP entries, the magnitude field (exponent field of
+// the high word, r^ from the high word, high word of an RN32 magnitude) and
+// the packing of the angle codes (Fig. comp_regimes).
+// <0,7,22>-17-18 (Sec. 3): E7 in bits 57..63 (E8 - 47), m22 in 35..56 (the
+// top 22 of the 23 mantissa bits), n_phi in 18..34, n_theta in 0..17.
+struct GeoPrimary {
   static constexpr int N = 262143, M = 131071;
   static constexpr int ST = 8, SP = 8, NT = 513, NP = 513;
   static constexpr int MAP = MAP_UNIFORM;
+  static constexpr uint32_t EALL = 127u;   // non-finite exponent field
+  __device__ static uint32_t efield(uint32_t hi) { return hi >> 25; }
+  __device__ static float mag(uint32_t hi) {
+    return __uint_as_float(((hi >> 2) & 0xFFFFFFFEu) + (47u << 23));
+  }
+  __device__ static uint32_t hi_of(uint32_t rb) { return ((rb - (47u << 23)) << 2) & 0xFFFFFFF8u; }
   __device__ static void unpack(uint32_t hi, uint32_t lo, uint32_t &nt, uint32_t &np) {
     nt = lo & 0x3FFFFu;
     np = __funnelshift_r(lo, hi, 18) & 0x1FFFFu;
@@ -43,11 +52,18 @@ struct GeoPrimary {  // <0,7,22>-17-18: n_phi in bits 18..34, n_theta in 0..17
 };
 
 // Fractional split (Sec. 2.4) at n_phi_max + 1 = 185363, n_theta_max + 1 =
-// floor(2^35 / 185363) = 185364: n_p = n_phi (N + 1) + n_theta in bits 0..34.
+// floor(2^35 / 185363) = 185364: the magnitude as in <0,7,22>-17-18 and
+// n_p = n_phi (N + 1) + n_theta in bits 0..34.
 struct GeoSplit {
   static constexpr int N = 185363, M = 185362;
   static constexpr int ST = 7, SP = 8, NT = 725, NP = 725;
   static constexpr int MAP = MAP_FRACSPLIT;
+  static constexpr uint32_t EALL = 127u;
+  __device__ static uint32_t efield(uint32_t hi) { return hi >> 25; }
+  __device__ static float mag(uint32_t hi) {
+    return __uint_as_float(((hi >> 2) & 0xFFFFFFFEu) + (47u << 23));
+  }
+  __device__ static uint32_t hi_of(uint32_t rb) { return ((rb - (47u << 23)) << 2) & 0xFFFFFFF8u; }
   __device__ static void unpack(uint32_t hi, uint32_t lo, uint32_t &nt, uint32_t &np) {
     const uint64_t npk = ((uint64_t)(hi & 7u) << 32) | lo;
     const uint64_t q = npk / (uint64_t)(N + 1);
@@ -62,18 +78,81 @@ struct GeoSplit {
   }
 };
 
+// <0,7,23>-17-17 (Sec. 2.3): E7 in bits 57..63, m23 in 34..56, n_phi in
+// 17..33, n_theta in 0..16.
+struct GeoL1717 {
+  static constexpr int N = 131071, M = 131071;
+  static constexpr int ST = 7, SP = 8, NT = 513, NP = 513;
+  static constexpr int MAP = MAP_UNIFORM;
+  static constexpr uint32_t EALL = 127u;
+  __device__ static uint32_t efield(uint32_t hi) { return hi >> 25; }
+  __device__ static float mag(uint32_t hi) { return __uint_as_float((hi >> 2) + (47u << 23)); }
+  __device__ static uint32_t hi_of(uint32_t rb) { return ((rb - (47u << 23)) << 2) & 0xFFFFFFFCu; }
+  __device__ static void unpack(uint32_t hi, uint32_t lo, uint32_t &nt, uint32_t &np) {
+    nt = lo & 0x1FFFFu;
+    np = __funnelshift_r(lo, hi, 17) & 0x1FFFFu;
+  }
+  __device__ static uint64_t pack(uint32_t hi_mag, int np, int nt) {
+    return ((uint64_t)(hi_mag | ((uint32_t)np >> 15)) << 32) |
+           (((uint32_t)np << 17) | (uint32_t)nt);
+  }
+};
+
+// <0,8,23>-16-17 (Sec. 2.3): the FP32 exponent and mantissa of RN32(r) in
+// bits 33..63 (E8 in 56..63), n_phi in 17..32, n_theta in 0..16.
+struct GeoL1617 {
+  static constexpr int N = 131071, M = 65535;
+  static constexpr int ST = 7, SP = 7, NT = 513, NP = 513;
+  static constexpr int MAP = MAP_UNIFORM;
+  static constexpr uint32_t EALL = 255u;
+  __device__ static uint32_t efield(uint32_t hi) { return hi >> 24; }
+  __device__ static float mag(uint32_t hi) { return __uint_as_float(hi >> 1); }
+  __device__ static uint32_t hi_of(uint32_t rb) { return (rb << 1) & 0xFFFFFFFEu; }
+  __device__ static void unpack(uint32_t hi, uint32_t lo, uint32_t &nt, uint32_t &np) {
+    nt = lo & 0x1FFFFu;
+    np = __funnelshift_r(lo, hi, 17) & 0xFFFFu;
+  }
+  __device__ static uint64_t pack(uint32_t hi_mag, int np, int nt) {
+    return ((uint64_t)(hi_mag | ((uint32_t)np >> 15)) << 32) |
+           (((uint32_t)np << 17) | (uint32_t)nt);
+  }
+};
+
+// Field positions of each fast layout, checked against a format.
+template <class G> struct GeoFields;
+template <> struct GeoFields<GeoPrimary> {
+  static constexpr uint32_t sh_phi = 18, sh_m = 35, sh_e = 57, mask_e = 127, mask_m = 0x3FFFFF;
+  static constexpr int e_off = -47;
+};
+template <> struct GeoFields<GeoSplit> {
+  static constexpr uint32_t sh_phi = 18, sh_m = 35, sh_e = 57, mask_e = 127, mask_m = 0x3FFFFF;
+  static constexpr int e_off = -47;
+};
+template <> struct GeoFields<GeoL1717> {
+  static constexpr uint32_t sh_phi = 17, sh_m = 34, sh_e = 57, mask_e = 127, mask_m = 0x7FFFFF;
+  static constexpr int e_off = -47;
+};
+template <> struct GeoFields<GeoL1617> {
+  static constexpr uint32_t sh_phi = 17, sh_m = 33, sh_e = 56, mask_e = 255, mask_m = 0x7FFFFF;
+  static constexpr int e_off = 0;
+};
+
 template <class G>
 __host__ __device__ inline bool is_geo(const DevFormat &F) {
-  return F.sh_phi == 18 && F.sh_m == 35 && F.sh_e == 57 && F.mask_e == 127u &&
-         F.mask_m == 0x3FFFFFu && F.e_off == -47 && F.N == G::N && F.M == G::M &&
-         F.st == G::ST && F.sp == G::SP && F.nent_t == G::NT && F.nent_p == G::NP &&
-         F.under_mode == 0 && F.over_mode == 0;
+  using P = GeoFields<G>;
+  return F.sh_phi == P::sh_phi && F.sh_m == P::sh_m && F.sh_e == P::sh_e &&
+         F.mask_e == P::mask_e && F.mask_m == P::mask_m && F.e_off == P::e_off &&
+         F.N == G::N && F.M == G::M && F.st == G::ST && F.sp == G::SP &&
+         F.nent_t == G::NT && F.nent_p == G::NP && F.under_mode == 0 && F.over_mode == 0;
 }
 
-// Which fast layout a format is: 1 primary, 2 fractional split, 0 none.
+// Which fast layout a format is: 1 primary, 2 fractional split, 3
+// <0,7,23>-17-17, 4 <0,8,23>-16-17, 0 none.
 __host__ __device__ inline int fast_geometry(int map, const DevFormat &F) {
   if (map == MAP_UNIFORM && is_geo<GeoPrimary>(F)) return 1;
   if (map == MAP_FRACSPLIT && is_geo<GeoSplit>(F)) return 2;
+  if (map == MAP_UNIFORM && is_geo<GeoL1717>(F)) return 3;
+  if (map == MAP_UNIFORM && is_geo<GeoL1617>(F)) return 4;
   return 0;
 }
 
@@ -196,12 +275,12 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry
                                         float2 &Y, float2 &Z, bool &slow0, bool &slow1) {
   const uint32_t hi0 = (uint32_t)(w0 >> 32), lo0 = (uint32_t)w0;
   const uint32_t hi1 = (uint32_t)(w1 >> 32), lo1 = (uint32_t)w1;
-  const uint32_t E0 = hi0 >> 25, E1 = hi1 >> 25;
-  // r^ bits: exponent E7 + 47, mantissa m22 << 1 (Sec. 2.3)
-  const float r0 = E0 == 0u ? 0.0f : __uint_as_float(((hi0 >> 2) & 0xFFFFFFFEu) + (47u << 23));
-  const float r1 = E1 == 0u ? 0.0f : __uint_as_float(((hi1 >> 2) & 0xFFFFFFFEu) + (47u << 23));
-  slow0 = (E0 == 127u);
-  slow1 = (E1 == 127u);
+  const uint32_t E0 = G::efield(hi0), E1 = G::efield(hi1);
+  // r^ from the magnitude field (Sec. 2.3); exponent field 0 is the zero vector
+  const float r0 = E0 == 0u ? 0.0f : G::mag(hi0);
+  const float r1 = E1 == 0u ? 0.0f : G::mag(hi1);
+  slow0 = (E0 == G::EALL);
+  slow1 = (E1 == G::EALL);
   // n_theta, n_phi as exact floats (magic-number conversion, codes < 2^23)
   uint32_t nt0, np0, nt1, np1;
   G::unpack(hi0, lo0, nt0, np0);
@@ -529,8 +608,8 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   if (nt0 == kN || np0 == 0 || np0 == kM) nt0 = 0;
   if (nt1 == kN || np1 == 0 || np1 == kM) nt1 = 0;
   const uint32_t rb0 = __float_as_uint(r32.x), rb1 = __float_as_uint(r32.y);
-  r.hi0 = ((rb0 - (47u << 23)) << 2) & 0xFFFFFFF8u;
-  r.hi1 = ((rb1 - (47u << 23)) << 2) & 0xFFFFFFF8u;
+  r.hi0 = G::hi_of(rb0);
+  r.hi1 = G::hi_of(rb1);
   r.w0 = G::pack(r.hi0, np0, nt0);
   r.w1 = G::pack(r.hi1, np1, nt1);
   r.fl0 = r.fl1 = 0u;

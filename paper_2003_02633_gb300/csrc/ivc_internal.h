@@ -26,8 +26,6 @@ enum KernelKind : int {
   K_BATCH_AXPY_FAST = 11,
   K_COMPRESS_FAST = 12,
   K_DECOMPRESS_FAST = 13,
-  K_GATHER = 14,
-  K_GATHER_FAST = 15,
 };
 
 struct LaunchShape {
@@ -92,10 +90,10 @@ cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, 
                                const LaunchShape &s, cudaStream_t st);
 cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P,
                            const LaunchShape &s, cudaStream_t st);
-// Gather-decompress; s.vec2 selects the fast kernel (16-byte aligned idx,
-// 8-byte aligned xyz, a fast layout).
+// Gather-decompress; pairs selects the two-per-thread kernel (16-byte aligned
+// idx, 8-byte aligned xyz) when the layout has a fast path.  Sizes its grid.
 cudaError_t launch_gather(int map, const DevFormat &F, const uint64_t *w, int64_t nw,
-                          const int64_t *idx, int64_t n, float *xyz, const LaunchShape &s,
+                          const int64_t *idx, int64_t n, float *xyz, bool pairs,
                           cudaStream_t st);
 cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,
                              cudaStream_t st);

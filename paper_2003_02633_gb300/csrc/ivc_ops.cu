@@ -510,66 +510,6 @@ __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ De
   if (!done && threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_TIMEOUT);
 }
 
-// Gather-decompress (random access, the motivation of Sec. 1): xyz[i] =
-// decompress(w[idx[i]]) for i < n, AoS output.  Indices outside [0, nw) read
-// nothing and give NaN components.  Generic kernel: one index per thread.
-template <int MAP>
-__global__ void __launch_bounds__(256) k_gather(const __grid_constant__ DevFormat F,
-                                                const uint64_t *__restrict__ w, int64_t nw,
-                                                const int64_t *__restrict__ idx, int64_t n,
-                                                float *xyz) {
-  IVC_TABLES(F, MAP);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int64_t j = __ldcs(idx + i);
-    float3 v = make_float3(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
-                           __int_as_float(0x7fc00000));
-    if ((uint64_t)j < (uint64_t)nw) v = decode_word<MAP>(__ldg(w + j), F, tab_t, tab_p);
-    __stcs(xyz + 3 * i, v.x);
-    __stcs(xyz + 3 * i + 1, v.y);
-    __stcs(xyz + 3 * i + 2, v.z);
-  }
-}
-
-// Fast-path gather: two indices per thread (16-byte index loads), packed
-// decode, the same AoS stores as k_decompress_fast.  Requires a 16-byte aligned
-// idx and an 8-byte aligned xyz.
-template <class G>
-__global__ void __launch_bounds__(256) k_gather_fast(const __grid_constant__ DevFormat F,
-                                                     const uint64_t *__restrict__ w, int64_t nw,
-                                                     const int64_t *__restrict__ idx, int64_t n,
-                                                     float *xyz) {
-  IVC_TABLES(F, G::MAP);
-  const int64_t n2 = n >> 1;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const longlong2 *i2 = reinterpret_cast<const longlong2 *>(idx);
-  float2 *v2 = reinterpret_cast<float2 *>(xyz);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-    const longlong2 jj = __ldcs(i2 + i);
-    const bool ok0 = (uint64_t)jj.x < (uint64_t)nw, ok1 = (uint64_t)jj.y < (uint64_t)nw;
-    const uint64_t w0 = ok0 ? __ldg(w + jj.x) : 0ull;
-    const uint64_t w1 = ok1 ? __ldg(w + jj.y) : 0ull;
-    float2 X, Y, Z;
-    fast::decode2_full<G>(w0, w1, F, tab_t, tab_p, X, Y, Z);
-    const float qn = __int_as_float(0x7fc00000);
-    if (!ok0) X.x = Y.x = Z.x = qn;
-    if (!ok1) X.y = Y.y = Z.y = qn;
-    __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
-    __stcs(v2 + 3 * i + 1, make_float2(Z.x, X.y));
-    __stcs(v2 + 3 * i + 2, make_float2(Y.y, Z.y));
-  }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    const int64_t i = n - 1;
-    const int64_t j = idx[i];
-    float3 v = make_float3(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
-                           __int_as_float(0x7fc00000));
-    if ((uint64_t)j < (uint64_t)nw) v = decode_word<G::MAP>(w[j], F, tab_t, tab_p);
-    xyz[3 * i] = v.x;
-    xyz[3 * i + 1] = v.y;
-    xyz[3 * i + 2] = v.z;
-  }
-}
-
 // Tiles per field and their prefix sums (one block; nfields is small).
 __global__ void k_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -633,22 +573,30 @@ cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t 
   IVC_DISPATCH_MAP(map, k_update, F, dt, v, f, rho, v_out, m_out, n);
 }
 
+// Fast launchers: the layout is read from F (the caller has checked
+// fast::fast_geometry()); f receives a value of the layout's type.
+template <class Fn>
+cudaError_t with_geo(const DevFormat &F, Fn f) {
+  if (fast::is_geo<fast::GeoSplit>(F))
+    f(fast::GeoSplit{});
+  else if (fast::is_geo<fast::GeoL1717>(F))
+    f(fast::GeoL1717{});
+  else if (fast::is_geo<fast::GeoL1617>(F))
+    f(fast::GeoL1617{});
+  else
+    f(fast::GeoPrimary{});
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P,
                            const LaunchShape &s, cudaStream_t st) {
-  const int geo = fast::fast_geometry(map, F);
-  if (geo != 0) {
-    if (op == IVC_OP_ADD) {
-      if (geo == 2)
-        k_batched_fast<IVC_OP_ADD, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, P);
+  if (fast::fast_geometry(map, F) != 0) {
+    return with_geo(F, [&](auto g) {
+      if (op == IVC_OP_ADD)
+        k_batched_fast<IVC_OP_ADD, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, P);
       else
-        k_batched_fast<IVC_OP_ADD, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, P);
-    } else {
-      if (geo == 2)
-        k_batched_fast<IVC_OP_AXPY, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, P);
-      else
-        k_batched_fast<IVC_OP_AXPY, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, P);
-    }
-    return cudaGetLastError();
+        k_batched_fast<IVC_OP_AXPY, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, P);
+    });
   }
   if (op == IVC_OP_ADD) {
     switch (map) {
@@ -666,70 +614,41 @@ cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P
   return cudaGetLastError();
 }
 
-// Fast launchers: the layout (primary or fractional split) is read from F;
-// the caller has checked fast::fast_geometry().
-#define IVC_FAST_GEO(F, CALL_PRIMARY, CALL_SPLIT) \
-  if (fast::is_geo<fast::GeoSplit>(F)) {         \
-    CALL_SPLIT;                                  \
-  } else {                                       \
-    CALL_PRIMARY;                                \
-  }                                              \
-  return cudaGetLastError()
-
 cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_t *b, uint64_t *c,
                             int64_t n, const LaunchShape &s, cudaStream_t st) {
-  IVC_FAST_GEO(
-      F,
-      (k_fused_fast<IVC_OP_ADD, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n,
-                                                                                 0.0f)),
-      (k_fused_fast<IVC_OP_ADD, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n,
-                                                                               0.0f)));
+  return with_geo(F, [&](auto g) {
+    k_fused_fast<IVC_OP_ADD, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n, 0.0f);
+  });
 }
 
 cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
                              int64_t n, const LaunchShape &s, cudaStream_t st) {
-  IVC_FAST_GEO(
-      F,
-      (k_fused_fast<IVC_OP_AXPY, fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n,
-                                                                                  alpha)),
-      (k_fused_fast<IVC_OP_AXPY, fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n,
-                                                                                alpha)));
+  return with_geo(F, [&](auto g) {
+    k_fused_fast<IVC_OP_AXPY, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n, alpha);
+  });
 }
 
 cudaError_t launch_compress_fast(const DevFormat &F, const float *xyz, int64_t n, uint64_t *w,
                                  ivc_counts *counts, const LaunchShape &s, cudaStream_t st) {
-  IVC_FAST_GEO(
-      F, (k_compress_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts)),
-      (k_compress_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts)));
+  return with_geo(F, [&](auto g) {
+    k_compress_fast<decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts);
+  });
 }
 
 cudaError_t launch_decompress_fast(const DevFormat &F, const uint64_t *w, int64_t n, float *xyz,
                                    const LaunchShape &s, cudaStream_t st) {
-  IVC_FAST_GEO(F, (k_decompress_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz)),
-               (k_decompress_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz)));
+  return with_geo(F, [&](auto g) {
+    k_decompress_fast<decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz);
+  });
 }
 
 cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, const uint64_t *f,
                                const float *rho, uint64_t *v_out, uint64_t *m_out, int64_t n,
                                const LaunchShape &s, cudaStream_t st) {
-  IVC_FAST_GEO(F,
-               (k_update_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(
-                   F, dt, v, f, rho, v_out, m_out, n)),
-               (k_update_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(
-                   F, dt, v, f, rho, v_out, m_out, n)));
-}
-
-cudaError_t launch_gather(int map, const DevFormat &F, const uint64_t *w, int64_t nw,
-                          const int64_t *idx, int64_t n, float *xyz, const LaunchShape &s,
-                          cudaStream_t st) {
-  if (s.vec2 && fast::fast_geometry(map, F) != 0) {
-    IVC_FAST_GEO(F,
-                 (k_gather_fast<fast::GeoPrimary><<<s.grid, s.block, s.smem, st>>>(F, w, nw, idx,
-                                                                                   n, xyz)),
-                 (k_gather_fast<fast::GeoSplit><<<s.grid, s.block, s.smem, st>>>(F, w, nw, idx, n,
-                                                                                 xyz)));
-  }
-  IVC_DISPATCH_MAP(map, k_gather, F, w, nw, idx, n, xyz);
+  return with_geo(F, [&](auto g) {
+    k_update_fast<decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, dt, v, f, rho, v_out, m_out,
+                                                               n);
+  });
 }
 
 cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int64_t *tile_start,
@@ -754,8 +673,6 @@ static const void *kernel_ptr(int kind) {
     case K_COMPRESS_FAST: return (const void *)k_compress_fast<fast::GeoPrimary>;
     case K_DECOMPRESS_FAST: return (const void *)k_decompress_fast<fast::GeoPrimary>;
     case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY, fast::GeoPrimary>;
-    case K_GATHER: return (const void *)k_gather<MAP>;
-    case K_GATHER_FAST: return (const void *)k_gather_fast<fast::GeoPrimary>;
     default: return (const void *)k_batched<MAP, IVC_OP_AXPY>;
   }
 }
