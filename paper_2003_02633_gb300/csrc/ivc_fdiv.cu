@@ -93,40 +93,58 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   }
 }
 
+// Rows of a chunk handled by one producer thread: the thread owns the element
+// pair e2 = pt % 32 of the rows r = pt / 32 + 8 t (t < kRowsPT), row r being
+// point jj = r / nvars, equation p = r % nvars of the chunk.  The same thread
+// copies and later decodes each of its items, so it waits only for its own
+// cp.async groups.
+constexpr int kRowsPT = (kJC * kMaxNv + kProducers / 32 - 1) / (kProducers / 32);
+
+struct ProdRows {
+  int e2;
+  int r[kRowsPT], jj[kRowsPT];
+};
+
+__device__ __forceinline__ ProdRows prod_rows(int pt, int nv) {
+  ProdRows m;
+  m.e2 = pt & (kTE / 2 - 1);
+#pragma unroll
+  for (int t = 0; t < kRowsPT; ++t) {
+    const int r = (pt >> 5) + (kProducers / 32) * t;
+    m.r[t] = r;
+    m.jj[t] = r / nv;
+  }
+  return m;
+}
+
 // Copies the raw data of one chunk (words, or FP32 components) into a raw
-// buffer: item q (two adjacent elements of row (jj, p)) at q * 2 words, or at
-// q * 6 floats (component-major pairs).  Each producer thread copies exactly
-// the items it decodes later, so only its own cp.async groups need waiting.
+// buffer: item q = r * 32 + e2 (two adjacent elements of row r) at q * 2
+// words, or at q * 6 floats (component-major pairs).
 template <int MODE>
 __device__ __forceinline__ void copy_chunk(uint32_t *Wb, const void *src, int64_t ld, int ns,
                                            int nv, int64_t ne, int64_t e0, int j0, int jn,
-                                           int pt) {
-  const int items = jn * nv * (kTE / 2);
-  for (int q = pt; q < items; q += kProducers) {
-    const int e2 = q & (kTE / 2 - 1);
-    const int r = q / (kTE / 2);
-    const int jj = r / nv, p = r - jj * nv;
-    const int64_t e = e0 + 2 * e2;
+                                           const ProdRows &m) {
+  const int64_t e = e0 + 2 * m.e2;
+  const bool in0 = e < ne, in1 = e + 1 < ne;
+#pragma unroll
+  for (int t = 0; t < kRowsPT; ++t) {
+    if (m.jj[t] >= jn) continue;
+    const int q = m.r[t] * (kTE / 2) + m.e2;
     if (MODE == FD_F32) {
       const float *Fr = static_cast<const float *>(src);
+      const int jp = (j0 + m.jj[t]) * nv + (m.r[t] - m.jj[t] * nv);   // row within a component
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int64_t base = (((int64_t)c * ns + j0 + jj) * nv + p) * ld + e;
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const bool in = e + t < ne;
-          cp_async<4>(Wb + q * 6 + c * 2 + t, in ? (const void *)(Fr + base + t) : src,
-                      in ? 4u : 0u);
-        }
+        const int64_t base = ((int64_t)c * ns * nv + jp) * ld + e;
+        cp_async<4>(Wb + q * 6 + c * 2, in0 ? (const void *)(Fr + base) : src, in0 ? 4u : 0u);
+        cp_async<4>(Wb + q * 6 + c * 2 + 1, in1 ? (const void *)(Fr + base + 1) : src,
+                    in1 ? 4u : 0u);
       }
     } else {
       const uint64_t *W = static_cast<const uint64_t *>(src);
-      const int64_t base = ((int64_t)(j0 + jj) * nv + p) * ld + e;
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const bool in = e + t < ne;
-        cp_async<8>(Wb + (q * 2 + t) * 2, in ? (const void *)(W + base + t) : src, in ? 8u : 0u);
-      }
+      const int64_t base = ((int64_t)j0 * nv + m.r[t]) * ld + e;
+      cp_async<8>(Wb + q * 4, in0 ? (const void *)(W + base) : src, in0 ? 8u : 0u);
+      cp_async<8>(Wb + q * 4 + 2, in1 ? (const void *)(W + base + 1) : src, in1 ? 8u : 0u);
     }
   }
   cp_async_commit();
@@ -170,12 +188,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x < kProducers) {
     // ------------------------------------------------------------ producers
-    const int pt = threadIdx.x;
+    const ProdRows m = prod_rows(threadIdx.x, nv);
     uint32_t g = 0;
     int64_t tile = blockIdx.x;
     int ch = 0;
     if (tile < ntiles)
-      copy_chunk<MODE>(Ws, src, ld, ns, nv, ne, tile * kTE, 0, min(kJC, ns), pt);
+      copy_chunk<MODE>(Ws, src, ld, ns, nv, ne, tile * kTE, 0, min(kJC, ns), m);
     while (tile < ntiles) {
       // start the copies of the next chunk, then wait for this chunk's
       int64_t ntile = tile;
@@ -186,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (ntile < ntiles)
         copy_chunk<MODE>(Ws + ((g + 1) & 1) * kWBuf, src, ld, ns, nv, ne, ntile * kTE,
-                         nch * kJC, min(kJC, ns - nch * kJC), pt);
+                         nch * kJC, min(kJC, ns - nch * kJC), m);
       else
         cp_async_commit();  // an empty group keeps "all but the newest" meaning this chunk
       cp_async_wait_1();
@@ -201,11 +219,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int jn = min(kJC, ns - ch * kJC);
       float *X = Xs + b * kXBuf;
       const uint32_t *Wb = Ws + b * kWBuf;
-      const int items = jn * nv * (kTE / 2);
-      for (int q = pt; q < items; q += kProducers) {
-        const int e2 = q & (kTE / 2 - 1);
-        const int r = q / (kTE / 2);
-        const int jj = r / nv, p = r - jj * nv;
+      // rows r0 + 8 t in increasing order (so are their points jj): a rolled
+      // loop keeps one copy of the decoder in the instruction stream
+      int rr = m.r[0], jr = m.jj[0], pr = m.r[0] - m.jj[0] * nv;
+#pragma unroll 1
+      for (int t = 0; t < kRowsPT && jr < jn; ++t) {
+        const int q = rr * (kTE / 2) + m.e2;
         float2 vx, vy, vz;
         if (MODE == FD_F32) {
           vx = *reinterpret_cast<const float2 *>(Wb + q * 6);
@@ -223,10 +242,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             vz = make_float2(a.z, c3.z);
           }
         }
-        float *xr = X + ((jj * kMaxNv + p) * 3) * kTE + 2 * e2;
+        float *xr = X + ((jr * kMaxNv + pr) * 3) * kTE + 2 * m.e2;
         *reinterpret_cast<float2 *>(xr) = vx;
         *reinterpret_cast<float2 *>(xr + kTE) = vy;
         *reinterpret_cast<float2 *>(xr + 2 * kTE) = vz;
+        rr += kProducers / 32;
+        pr += kProducers / 32;
+        while (pr >= nv) {
+          pr -= nv;
+          ++jr;
+        }
       }
       mbar_arrive(bars + b);
       tile = ntile;
