@@ -282,18 +282,20 @@ ivc_status ivc_f32_flux_divergence(const float *F, int64_t ld, int ns, int nvars
                                    ivc_stream_t stream);
 
 /* The compressed add c = a + b (Sec. 5) of HOST-resident words: a, b, c are
- * host pointers (page-locked memory lets the copies overlap with the
- * kernels; pageable memory works but serialises).  The words stream through
- * the caller's device `workspace` (16-byte aligned, ws_bytes long) in chunks
- * of floor(ws_bytes / 72) & ~1 vectors, three chunks in flight on streams of
- * the library's own, so that host-to-device copies, kernels and
- * device-to-host copies of consecutive chunks overlap.  The work starts after
- * what is already queued on `stream`, and `stream` waits for all of it: the
- * host buffers and the workspace must stay valid until `stream` completes.
- * Results are those of ivc_add.  Errors: IVC_ERR_ARG (NULL pointers, n < 0),
- * IVC_ERR_ALIGN (host pointers not 8-byte, workspace not 16-byte aligned),
- * IVC_ERR_NOMEM (workspace below 144 bytes), IVC_ERR_CUDA; on an error,
- * chunks already queued may still run. */
+ * host pointers.  When all three are page-locked (cudaHostAlloc or
+ * registered), the kernel reads and writes them directly over the host link
+ * on `stream` and the workspace is not used (may be NULL).  Otherwise the
+ * words stream through the caller's device `workspace` (16-byte aligned,
+ * ws_bytes long) in chunks of floor(ws_bytes / 72) & ~1 vectors, three chunks
+ * in flight on streams of the library's own, so that host-to-device copies,
+ * kernels and device-to-host copies of consecutive chunks overlap.  The work
+ * starts after what is already queued on `stream`, and `stream` waits for all
+ * of it: the host buffers and the workspace must stay valid until `stream`
+ * completes.  Results are those of ivc_add.  Errors: IVC_ERR_ARG (NULL
+ * pointers, n < 0, no workspace for pageable memory), IVC_ERR_ALIGN (host
+ * pointers not 8-byte, workspace not 16-byte aligned), IVC_ERR_NOMEM
+ * (workspace below 144 bytes), IVC_ERR_CUDA; on an error, chunks already
+ * queued may still run. */
 ivc_status ivc_add_host(const ivc_format *fmt, const uint64_t *a, const uint64_t *b,
                         uint64_t *c, int64_t n, void *workspace, size_t ws_bytes,
                         ivc_stream_t stream);

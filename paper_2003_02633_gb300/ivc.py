@@ -239,18 +239,18 @@ def f32_flux_divergence(F, D, ne=None, out=None, stream=None):
     return out
 
 
-def add_host(fmt, a, b, out, workspace, stream=None):
-    """ivc_add_host: c = a + b for int64 word tensors in (pinned) host memory,
-    streamed through the device tensor ``workspace`` (any dtype, 16-byte
-    aligned) in chunks.  Asynchronous on ``stream``: synchronise before reading
-    ``out``."""
+def add_host(fmt, a, b, out, workspace=None, stream=None):
+    """ivc_add_host: c = a + b for int64 word tensors in host memory.  Pinned
+    tensors are read and written by the kernel directly; pageable ones stream
+    through the device tensor ``workspace`` (any dtype, 16-byte aligned) in
+    chunks.  Asynchronous on ``stream``: synchronise before reading ``out``."""
     for t in (a, b, out):
         if t.is_cuda or not t.is_contiguous():
             raise ValueError("add_host expects contiguous host tensors")
+    ws_ptr = _ptr(workspace) if workspace is not None else None
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _chk(load().ivc_add_host(ctypes.byref(fmt), a.data_ptr(), b.data_ptr(), out.data_ptr(),
-                             a.shape[0], _ptr(workspace),
-                             workspace.numel() * workspace.element_size(), _stream(stream)),
-         "ivc_add_host")
+                             a.shape[0], ws_ptr, ws_bytes, _stream(stream)), "ivc_add_host")
     return out
 
 

@@ -334,6 +334,31 @@ def test_add_host_streams_chunks(c0, ws_vectors):
     assert mism <= allowed_mismatches(n)
 
 
+def test_add_host_pageable_staged(c0):
+    """Pageable host words take the staged path (chunks through the workspace)."""
+    fo, fg = formats("primary")
+    wa, wb = O.compress(fo, c0[0]), O.compress(fo, c0[1])
+    n = wa.shape[0]
+    hc = torch.zeros(n, dtype=torch.int64)
+    ws = torch.empty(3 * 3 * 4096, dtype=torch.int64, device=DEV)
+    ivc.add_host(fg, torch.from_numpy(wa.view(np.int64)), torch.from_numpy(wb.view(np.int64)),
+                 hc, ws)
+    torch.cuda.synchronize()
+    assert int(np.sum(hc.numpy().view(np.uint64) != O.add(fo, wa, wb))) <= allowed_mismatches(n)
+
+
+def test_add_host_pinned_without_workspace(c0):
+    fo, fg = formats("primary")
+    wa, wb = O.compress(fo, c0[0]), O.compress(fo, c0[1])
+    n = wa.shape[0]
+    ha = torch.from_numpy(wa.view(np.int64)).pin_memory()
+    hb = torch.from_numpy(wb.view(np.int64)).pin_memory()
+    hc = torch.zeros(n, dtype=torch.int64).pin_memory()
+    ivc.add_host(fg, ha, hb, hc)     # zero-copy: no workspace needed
+    torch.cuda.synchronize()
+    assert int(np.sum(hc.numpy().view(np.uint64) != O.add(fo, wa, wb))) <= allowed_mismatches(n)
+
+
 def test_add_host_tiny_chunks():
     fo, fg = formats("primary")
     a, b = synth.roundtrip_inputs(101, seed=5)
