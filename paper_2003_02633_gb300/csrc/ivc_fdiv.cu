@@ -36,6 +36,9 @@ constexpr int kThreads = kProducers + kConsumers;
 constexpr int kXBuf = kJC * kMaxNv * 3 * kTE;   // floats per decoded buffer
 constexpr int kWBuf = kJC * kMaxNv * kTE * 3;   // 32-bit units per raw buffer (FP32 rows)
 constexpr long long kWaitCycles = 2000000000ll; // about a second
+// the consumers cover 64 points (16 groups of 4) x the tile's elements (groups of 4)
+static_assert(kConsumers == 16 * (kTE / 4), "consumer mapping");
+static_assert(kProducers % (kTE / 2) == 0, "producer mapping");
 
 enum : int { FD_GENERIC = 0, FD_FAST = 1, FD_F32 = 2 };
 
@@ -94,11 +97,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Rows of a chunk handled by one producer thread: the thread owns the element
-// pair e2 = pt % 32 of the rows r = pt / 32 + 8 t (t < kRowsPT), row r being
+// pair e2 = pt % (kTE / 2) of the rows r = pt / (kTE / 2) + kRowsPass t
+// (t < kRowsPT), row r being
 // point jj = r / nvars, equation p = r % nvars of the chunk.  The same thread
 // copies and later decodes each of its items, so it waits only for its own
 // cp.async groups.
-constexpr int kRowsPT = (kJC * kMaxNv + kProducers / 32 - 1) / (kProducers / 32);
+constexpr int kRowsPass = kProducers / (kTE / 2);   // rows the producers cover per pass
+constexpr int kRowsPT = (kJC * kMaxNv + kRowsPass - 1) / kRowsPass;
 
 struct ProdRows {
   int e2;
@@ -110,7 +115,7 @@ __device__ __forceinline__ ProdRows prod_rows(int pt, int nv) {
   m.e2 = pt & (kTE / 2 - 1);
 #pragma unroll
   for (int t = 0; t < kRowsPT; ++t) {
-    const int r = (pt >> 5) + (kProducers / 32) * t;
+    const int r = pt / (kTE / 2) + kRowsPass * t;
     m.r[t] = r;
     m.jj[t] = r / nv;
   }
@@ -246,8 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         *reinterpret_cast<float2 *>(xr) = vx;
         *reinterpret_cast<float2 *>(xr + kTE) = vy;
         *reinterpret_cast<float2 *>(xr + 2 * kTE) = vz;
-        rr += kProducers / 32;
-        pr += kProducers / 32;
+        rr += kRowsPass;
+        pr += kRowsPass;
         while (pr >= nv) {
           pr -= nv;
           ++jr;
@@ -263,8 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   // -------------------------------------------------------------- consumers
   const int ct = threadIdx.x - kProducers;
-  const int eg = ct & 15;   // elements 4 eg .. 4 eg + 3 of the tile
-  const int kg = ct >> 4;   // points 4 kg .. 4 kg + 3
+  const int eg = ct % (kTE / 4);   // elements 4 eg .. 4 eg + 3 of the tile
+  const int kg = ct / (kTE / 4);   // points 4 kg .. 4 kg + 3
   const bool kact = 4 * kg < nsp;
   uint32_t g = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
