@@ -77,6 +77,37 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
 
 
+def issue_roofline(prof, gvec_s, clocks):
+    """The bound the compressed add actually meets: warp instructions issued per
+    second (instructions per vector from the committed ncu capture of the same
+    kernel sources x vectors per second) against the SMs' issue rate (4
+    schedulers per SM, one warp instruction per cycle each, at the sampled
+    maximum SM clock)."""
+    if not prof or "warp_inst_per_vector" not in prof:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * 4 * mhz * 1e6 / 1e9
+    achieved = gvec_s * prof["warp_inst_per_vector"]
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "warp_inst_per_vector": prof["warp_inst_per_vector"],
+            "source": "ncu smsp__inst_executed.sum of the same kernel sources (profiles/)"}
+
+
+def ncu_profile_entry(kernel: str):
+    """The committed ncu figures of a kernel, or None when its sources changed
+    since they were captured."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            e = json.load(f)[kernel]
+        return e if e.get("source_hash") == kernel_source_hash() else None
+    except Exception:
+        return None
+
+
 def ncu_traffic(kernel: str, n: int):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel source changed since it was captured."""
@@ -251,6 +282,7 @@ def run_ivc(args):
     hbm_peak, peak_src = measured_peaks()
     achieved = BYTES_PER_VEC * n / (kernel_ms * 1e-3) / 1e9
     traffic = ncu_traffic("ivc_add", n)
+    prof = ncu_profile_entry("ivc_add")
 
     # End to end through the public API: pinned host words in, result out.
     h_a = torch.empty(n, dtype=torch.int64, pin_memory=True)
@@ -298,6 +330,7 @@ def run_ivc(args):
                          "traffic": traffic, "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": BYTES_PER_VEC * n,
                          "kernel_ms": round(kernel_ms, 5)},
+            "issue_roofline": issue_roofline(prof, value, clocks),
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
                     "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n,
                     "matches_device_result": same,
