@@ -534,15 +534,15 @@ static __device__ __noinline__ float3 decode_generic(uint64_t w, const DevFormat
 // exact tests need.
 struct Enc2 {
   uint64_t w0, w1;         // words (provisional where pend != 0)
-  uint32_t fl0, fl1;       // range events (bit 0 overflow, 1 underflow, 2 NaN)
-  uint32_t pend0, pend1;   // pending kinds: bit 0 theta, bit 1 phi
+  uint32_t pend0, pend1;   // pending: bit 0 theta test, bit 1 phi test, bit 2 generic encode
   int nt0, nt1, np0, np1;  // k of a pending kind, else the code
   uint32_t hi0, hi1;       // high words without the n_phi bits
 };
 
-// Encodes two vectors.  The word of a vector with a pending exact decision
-// is provisional: the caller queues it with push2.  Range events (fl0 / fl1)
-// come only from vectors on the generic path.
+// Encodes two vectors.  The word of a vector with a pending exact decision,
+// or outside the fast path's magnitude window (zero, tiny, huge, Inf, NaN:
+// the generic encoder, with its range handling and events), is provisional:
+// the caller queues it with push2.
 template <class G>
 __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevFormat &F,
                                         const TabEntry *__restrict__ tab_t,
@@ -603,8 +603,8 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   int np0 = kp0 + (frp.x >= 0.5f ? 1 : 0), np1 = kp1 + (frp.y >= 0.5f ? 1 : 0);
   // pending exact decisions: kinds within kEps of a rounding boundary
   // (bit 0 theta, bit 1 phi); their words are provisional
-  r.pend0 = gen0 ? 0u : (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
-  r.pend1 = gen1 ? 0u : (fabsf(frt.y - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 2u : 0u);
+  r.pend0 = gen0 ? 4u : (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
+  r.pend1 = gen1 ? 4u : (fabsf(frt.y - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 2u : 0u);
   r.nt0 = (r.pend0 & 1u) ? kt0 : nt0;
   r.nt1 = (r.pend1 & 1u) ? kt1 : nt1;
   r.np0 = (r.pend0 & 2u) ? kp0 : np0;
@@ -617,9 +617,6 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   r.hi1 = G::hi_of(rb1);
   r.w0 = G::pack(r.hi0, np0, nt0);
   r.w1 = G::pack(r.hi1, np1, nt1);
-  r.fl0 = r.fl1 = 0u;
-  if (gen0) r.w0 = encode_generic<G::MAP>(x.x, y.x, z.x, F, tab_t, tab_p, r.fl0);
-  if (gen1) r.w1 = encode_generic<G::MAP>(x.y, y.y, z.y, F, tab_t, tab_p, r.fl1);
   return r;
 }
 
@@ -637,7 +634,18 @@ struct PendItem {
   float x, y, z;   // the encoded vector
   uint32_t hi;     // high word without the n_phi bits
   int nt;          // theta: k when pending, else the code
-  uint32_t npp;    // phi: k when pending, else the code (bits 0..29); kinds (bits 30..31)
+  uint32_t npp;    // phi: k when pending, else the code (bits 0..28); pending bits (29..31)
+};
+
+// Range events of the generic encoder, per thread (bit 0 overflow, 1
+// underflow, 2 NaN of its flags).
+struct Events {
+  uint32_t o = 0, u = 0, q = 0;
+  __device__ __forceinline__ void add(uint32_t flags) {
+    o += flags & 1u;
+    u += (flags >> 1) & 1u;
+    q += (flags >> 2) & 1u;
+  }
 };
 
 struct WarpQueue {
@@ -653,14 +661,21 @@ __device__ __forceinline__ WarpQueue warp_queue(void *base) {
 }
 
 // Runs once per 32 queued items: kept out of line so that the main loop's
-// register allocation does not carry the exact test.
+// register allocation does not carry the exact test or the generic encoder.
+// Returns the generic encoder's range events (0 for an exact test).
 template <class G>
-static __device__ __noinline__ void resolve_item(const PendItem *pit, const DevFormat &F,
-                                                 const TabEntry *tab_t, const TabEntry *tab_p) {
+static __device__ __noinline__ uint32_t resolve_item(const PendItem *pit, const DevFormat &F,
+                                                     const TabEntry *tab_t,
+                                                     const TabEntry *tab_p) {
   const PendItem it = *pit;
+  const uint32_t pend = it.npp >> 29;
+  if (pend & 4u) {
+    uint32_t flags = 0;
+    *it.dst = encode_generic<G::MAP>(it.x, it.y, it.z, F, tab_t, tab_p, flags);
+    return flags;
+  }
   int nt = it.nt;
-  int np = (int)(it.npp & 0x3FFFFFFFu);
-  const uint32_t pend = it.npp >> 30;
+  int np = (int)(it.npp & 0x1FFFFFFFu);
   // one kind-agnostic test per item; a second only when both kinds wait
   const int kind = (pend & 1u) ? 0 : 1;
   const int side = exact_side<G>(kind, kind ? np : nt, it.x, it.y, it.z, F, tab_t, tab_p);
@@ -669,6 +684,7 @@ static __device__ __noinline__ void resolve_item(const PendItem *pit, const DevF
   if (pend == 3u) np += exact_side<G>(1, np, it.x, it.y, it.z, F, tab_t, tab_p);
   if (nt == G::N || np == 0 || np == G::M) nt = 0;
   *it.dst = G::pack(it.hi, np, nt);
+  return 0u;
 }
 
 // Queues the pending vectors of one encode2 result (element 0 -> dst0,
@@ -677,7 +693,8 @@ static __device__ __noinline__ void resolve_item(const PendItem *pit, const DevF
 template <class G>
 __device__ __forceinline__ void push2(WarpQueue &wq, bool act, const Enc2 &e, float2 x, float2 y,
                                       float2 z, uint64_t *dst0, const DevFormat &F,
-                                      const TabEntry *tab_t, const TabEntry *tab_p) {
+                                      const TabEntry *tab_t, const TabEntry *tab_p,
+                                      Events *ev = nullptr) {
   const uint32_t p0 = act ? e.pend0 : 0u, p1 = act ? e.pend1 : 0u;
   const unsigned b0 = __ballot_sync(0xffffffffu, p0 != 0u);
   const unsigned b1 = __ballot_sync(0xffffffffu, p1 != 0u);
@@ -685,15 +702,16 @@ __device__ __forceinline__ void push2(WarpQueue &wq, bool act, const Enc2 &e, fl
   const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
   int slot = wq.count + __popc(b0 & lt) + __popc(b1 & lt);
   if (p0) {
-    wq.q[slot++] = PendItem{dst0, x.x, y.x, z.x, e.hi0, e.nt0, (uint32_t)e.np0 | (p0 << 30)};
+    wq.q[slot++] = PendItem{dst0, x.x, y.x, z.x, e.hi0, e.nt0, (uint32_t)e.np0 | (p0 << 29)};
   }
   if (p1) {
-    wq.q[slot] = PendItem{dst0 + 1, x.y, y.y, z.y, e.hi1, e.nt1, (uint32_t)e.np1 | (p1 << 30)};
+    wq.q[slot] = PendItem{dst0 + 1, x.y, y.y, z.y, e.hi1, e.nt1, (uint32_t)e.np1 | (p1 << 29)};
   }
   wq.count += __popc(b0) + __popc(b1);
   while (wq.count >= 32) {
     __syncwarp();
-    resolve_item<G>(wq.q + wq.count - 32 + (threadIdx.x & 31), F, tab_t, tab_p);
+    const uint32_t fl = resolve_item<G>(wq.q + wq.count - 32 + (threadIdx.x & 31), F, tab_t, tab_p);
+    if (ev) ev->add(fl);
     wq.count -= 32;
     __syncwarp();
   }
@@ -702,11 +720,12 @@ __device__ __forceinline__ void push2(WarpQueue &wq, bool act, const Enc2 &e, fl
 // Resolves what is left in the queue (all lanes call it).
 template <class G>
 __device__ __forceinline__ void drain(WarpQueue &wq, const DevFormat &F, const TabEntry *tab_t,
-                                      const TabEntry *tab_p) {
+                                      const TabEntry *tab_p, Events *ev = nullptr) {
   if (wq.count == 0) return;
   __syncwarp();
   if ((int)(threadIdx.x & 31) < wq.count) {
-    resolve_item<G>(wq.q + (threadIdx.x & 31), F, tab_t, tab_p);
+    const uint32_t fl = resolve_item<G>(wq.q + (threadIdx.x & 31), F, tab_t, tab_p);
+    if (ev) ev->add(fl);
   }
   wq.count = 0;
   __syncwarp();

@@ -20,14 +20,7 @@ namespace ivc {
 #define IVC_QUEUE(F) ((void *)(ivc_smem_tab + (F).nent_t + (F).nent_p))
 
 // Per-thread range-event counters (overflow, underflow, NaN).
-struct Events {
-  uint32_t o = 0, u = 0, q = 0;
-  __device__ __forceinline__ void add(uint32_t flags) {
-    o += flags & 1u;
-    u += (flags >> 1) & 1u;
-    q += (flags >> 2) & 1u;
-  }
-};
+using Events = fast::Events;
 
 // Sums the counters over the warp and adds them to the device counts.
 __device__ __forceinline__ void flush_counts(const Events &ev, ivc_counts *counts) {
@@ -309,14 +302,11 @@ __global__ void __launch_bounds__(256, 3) k_compress_fast(const __grid_constant_
     const float2 vx = make_float2(p0.x, p1.y), vy = make_float2(p0.y, p2.x),
                  vz = make_float2(p1.x, p2.y);
     const fast::Enc2 e = fast::encode2<G>(vx, vy, vz, F, tab_t, tab_p);
-    if (act) {
-      __stcs(w2 + i, make_ulonglong2(e.w0, e.w1));
-      ev.add(e.fl0);
-      ev.add(e.fl1);
-    }
-    fast::push2<G>(wq, act, e, vx, vy, vz, w + 2 * i, F, tab_t, tab_p);
+    if (act) __stcs(w2 + i, make_ulonglong2(e.w0, e.w1));
+    // vectors outside the fast window are encoded (and counted) by the queue
+    fast::push2<G>(wq, act, e, vx, vy, vz, w + 2 * i, F, tab_t, tab_p, &ev);
   }
-  fast::drain<G>(wq, F, tab_t, tab_p);
+  fast::drain<G>(wq, F, tab_t, tab_p, &ev);
   if ((n & 1) && warp == 0 && lane == 0) {
     const int64_t i = n - 1;
     uint32_t f = 0;
