@@ -582,8 +582,10 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
     nslow0 = (hu0 - fabsf(dev.x) <= kNormAmbig * r32.x) || ((__float_as_uint(r32.x) & 0x7fffffu) == 0u);
     nslow1 = (hu1 - fabsf(dev.y) <= kNormAmbig * r32.y) || ((__float_as_uint(r32.y) & 0x7fffffu) == 0u);
   }
-  if (nslow0 && !gen0) r32.x = norm_rn_f64(x.x, y.x, z.x);
-  if (nslow1 && !gen1) r32.y = norm_rn_f64(x.y, y.y, z.y);
+  // a magnitude within the norm's error bound of an FP32 rounding boundary
+  // (about 2^-18 of the vectors) is settled by the generic encoder, through
+  // the queue like the out-of-window vectors
+  const bool gq0 = gen0 || nslow0, gq1 = gen1 || nslow1;
   // angle estimates
   const Est2 e = estimate2<G>(x, y, z, r2h, r2l);
   // k = floor(t) clamped to [0, n_max - 1]; the fraction absorbs the clamp
@@ -603,8 +605,8 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   int np0 = kp0 + (frp.x >= 0.5f ? 1 : 0), np1 = kp1 + (frp.y >= 0.5f ? 1 : 0);
   // pending exact decisions: kinds within kEps of a rounding boundary
   // (bit 0 theta, bit 1 phi); their words are provisional
-  r.pend0 = gen0 ? 4u : (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
-  r.pend1 = gen1 ? 4u : (fabsf(frt.y - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 2u : 0u);
+  r.pend0 = gq0 ? 4u : (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
+  r.pend1 = gq1 ? 4u : (fabsf(frt.y - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 2u : 0u);
   r.nt0 = (r.pend0 & 1u) ? kt0 : nt0;
   r.nt1 = (r.pend1 & 1u) ? kt1 : nt1;
   r.np0 = (r.pend0 & 2u) ? kp0 : np0;
