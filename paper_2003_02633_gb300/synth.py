@@ -350,3 +350,198 @@ def tgv_euler_flux(elements_per_axis: int = 96, order: int = 3, p0: float = 100.
                 (Et + p)[:, None] * vel]
         out[j] = torch.stack(rows, dim=0).to(torch.float32)
     return out
+
+
+# ----------------------------------------------------------------------------
+# Flux-reconstruction element data for the steps of Table fr_nse (Sec. 4)
+
+
+def fr_basis(order: int = 3) -> dict:
+    """One-dimensional flux-reconstruction basis on the order+1 Gauss-Legendre
+    points xi_i of [-1, 1] (Sec. 4: tensor-product Gauss-Legendre solution and
+    flux points), FP64:
+      xg  the points;
+      dm  dm[i, a] = l_a'(xi_i), derivative of the Lagrange basis function a;
+      lm, lp  l_a(-1), l_a(+1): interpolation to the two ends;
+      gl, gr  g_L'(xi_i), g_R'(xi_i): derivatives of the DG correction
+              functions (right and left Radau polynomials of degree order+1,
+              g_L(-1) = 1, g_L(1) = 0, g_R(xi) = g_L(-xi))."""
+    q = order + 1
+    xg, _ = np.polynomial.legendre.leggauss(q)
+    P = np.polynomial.polynomial
+    dm = np.zeros((q, q))
+    lm = np.zeros(q)
+    lp = np.zeros(q)
+    for a in range(q):
+        others = np.delete(xg, a)
+        coef = P.polyfromroots(others) / np.prod(xg[a] - others)
+        dm[:, a] = P.polyval(xg, P.polyder(coef))
+        lm[a] = P.polyval(-1.0, coef)
+        lp[a] = P.polyval(1.0, coef)
+    L = np.polynomial.legendre
+    ek = np.zeros(q + 1)
+    ek[order] = 1.0
+    ek1 = np.zeros(q + 1)
+    ek1[order + 1] = 1.0
+    sgn = (-1.0) ** (order + 1) / 2.0
+    gL = sgn * (ek1 - ek)                      # Legendre coefficients of g_L
+    gl = L.legval(xg, L.legder(gL))
+    gr = -L.legval(-xg, L.legder(gL))           # g_R(xi) = g_L(-xi)
+    return {"order": order, "xg": xg, "dm": dm, "lm": lm, "lp": lp, "gl": gl, "gr": gr}
+
+
+def fr_face_points(order: int):
+    """Flux-point numbering of a hex: face = 2 c + s (axis c = 0, 1, 2 for x,
+    y, z; side s = 0 at xi_c = -1, 1 at +1), point f = face q^2 + b q + a with
+    (a, b) the point's indices along the other two axes in increasing order.
+    Returns an (nf, 3) int array of per-axis indices with -1 / q standing for
+    the ends xi_c = -1 / +1, and the (nf,) face of each point."""
+    q = order + 1
+    pts, face = [], []
+    for c in range(3):
+        oth = [d for d in range(3) if d != c]
+        for s in range(2):
+            for b in range(q):
+                for a in range(q):
+                    ijk = [0, 0, 0]
+                    ijk[c] = -1 if s == 0 else q
+                    ijk[oth[0]] = a
+                    ijk[oth[1]] = b
+                    pts.append(ijk)
+                    face.append(2 * c + s)
+    return np.array(pts), np.array(face)
+
+
+def _euler_rows_t(qv, gamma):
+    """Inviscid flux rows (5, ..., 3) of conserved q (5, ...) (Eq. eulerF)."""
+    import torch
+    rho = qv[0]
+    u = torch.stack([qv[1] / rho, qv[2] / rho, qv[3] / rho], dim=-1)
+    p = (gamma - 1.0) * (qv[4] - 0.5 * rho * (u * u).sum(-1))
+    rows = [qv[0][..., None] * u]
+    for i in range(3):
+        r = qv[1 + i][..., None] * u
+        r[..., i] = r[..., i] + p
+        rows.append(r)
+    rows.append((qv[4] + p)[..., None] * u)
+    return torch.stack(rows, dim=0)
+
+
+def fr_case(dims=(4, 4, 4), order: int = 3, deform: float = 0.1, perturb: float = 0.05,
+            p0: float = 100.0, rho0: float = 1.0, u0: float = 1.0, gamma: float = 1.4,
+            device="cpu") -> dict:
+    """Element data of the flux-reconstruction steps 5-11 of Table fr_nse on a
+    periodic mesh of Ex x Ey x Ez hexes covering [-pi, pi]^3, mapped by
+    x = P + deform (sin Py sin Pz, sin Pz sin Px, sin Px sin Py) (a smooth
+    periodic deformation of the uniform mesh; 0 gives the uniform mesh of the
+    paper's Taylor-Green runs).  Element e = (ez Ey + ey) Ex + ex.
+
+    Flow: the Taylor-Green vortex initial state (Sec. 4.2, p0 = 100) plus a
+    smooth periodic perturbation of relative size `perturb` in every primitive
+    (so that no gradient row is identically zero, as in the developed flow):
+      u = u0 (sin X cos Y cos Z + perturb sin(Y + Z)),
+      v = u0 (-cos X sin Y cos Z + perturb sin(Z + X)),
+      w = u0 perturb sin(X + Y),
+      p = p0 + rho0 u0^2 ((cos 2X + cos 2Y)(2 + cos 2Z) / 16 + perturb cos(X + Y + Z)),
+      rho = p rho0 / p0.
+
+    Returns FP32 torch tensors on `device` (FP64 arithmetic), element index
+    fastest; "row" tensors hold 3-vectors in the last axis:
+      w_s  (ns, 5, ne)     primitives rho, u, v, w, p at the solution points
+      q_s  (ns, 5, ne)     conserved rho, rho u, rho v, rho w, E
+      S_s  (ns, 3, ne, 3)  rows of S = |J| J^-1 (J = dx/dxi), the metric terms
+      detJ_s (ns, ne)      |J|
+      q_f, S_f, detJ_f     the same at the flux points (nf in place of ns)
+      n_f  (nf, 1, ne, 3)  scaled outward normal, sign(side) * row c of S
+      dw_f (nf, 5, ne)     jump w(x_f) - (interpolated w^s) of the primitives
+      nFinv_f (nf, 5, ne)  n_f . F_inv(q_f), the inviscid normal flux
+    plus "dims", "order", "gamma"."""
+    import torch
+    dev = torch.device(device)
+    Ex, Ey, Ez = dims
+    ne = Ex * Ey * Ez
+    B = fr_basis(order)
+    q = order + 1
+    ns = q ** 3
+    xg = B["xg"]
+    e = torch.arange(ne, device=dev, dtype=torch.int64)
+    eidx = [e % Ex, (e // Ex) % Ey, e // (Ex * Ey)]
+    hs = [2.0 * math.pi / Ex, 2.0 * math.pi / Ey, 2.0 * math.pi / Ez]
+    t64 = dict(device=dev, dtype=torch.float64)
+
+    def ref_coord(idx):                    # index -1 / q = end, else GL point
+        if idx < 0:
+            return -1.0
+        if idx >= q:
+            return 1.0
+        return float(xg[idx])
+
+    def geometry(ijk):
+        """Mapped coordinates (3, npts, ne), S (npts, 3, ne, 3), |J| (npts, ne)."""
+        npts = len(ijk)
+        xi = torch.tensor([[ref_coord(i) for i in p] for p in ijk], **t64)   # (npts, 3)
+        P = [(-math.pi + hs[c] * (eidx[c].double()[None, :] + 0.5)
+              + 0.5 * hs[c] * xi[:, c:c + 1]) for c in range(3)]            # (npts, ne)
+        sx, sy, sz = torch.sin(P[0]), torch.sin(P[1]), torch.sin(P[2])
+        cx, cy, cz = torch.cos(P[0]), torch.cos(P[1]), torch.cos(P[2])
+        A = deform
+        X = [P[0] + A * sy * sz, P[1] + A * sz * sx, P[2] + A * sx * sy]
+        one = torch.ones_like(sx)
+        dM = [[one, A * cy * sz, A * sy * cz],
+              [A * sz * cx, one, A * cz * sx],
+              [A * cx * sy, A * sx * cy, one]]
+        J = torch.stack([torch.stack([dM[i][j] * (0.5 * hs[j]) for j in range(3)], -1)
+                         for i in range(3)], -2)                            # (npts, ne, 3, 3)
+        det = torch.linalg.det(J)
+        S = det[..., None, None] * torch.linalg.inv(J)                     # rows of |J| J^-1
+        return X, S.permute(0, 2, 1, 3).contiguous(), det
+
+    def flow(X):
+        x, y, z = X
+        u = u0 * (torch.sin(x) * torch.cos(y) * torch.cos(z) + perturb * torch.sin(y + z))
+        v = u0 * (-torch.cos(x) * torch.sin(y) * torch.cos(z) + perturb * torch.sin(z + x))
+        w = u0 * perturb * torch.sin(x + y)
+        p = p0 + rho0 * u0 * u0 * ((torch.cos(2 * x) + torch.cos(2 * y)) * (2 + torch.cos(2 * z))
+                                   / 16.0 + perturb * torch.cos(x + y + z))
+        rho = p * rho0 / p0
+        prim = torch.stack([rho, u, v, w, p], 0)                           # (5, npts, ne)
+        En = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+        cons = torch.stack([rho, rho * u, rho * v, rho * w, En], 0)
+        return prim, cons
+
+    sol = [[jx, jy, jz] for jz in range(q) for jy in range(q) for jx in range(q)]
+    Xs, S_s, det_s = geometry(sol)
+    w_s, q_s = flow(Xs)
+    fpts, face = fr_face_points(order)
+    Xf, S_f, det_f = geometry(fpts.tolist())
+    w_f, q_f = flow(Xf)
+    nf = len(fpts)
+    # scaled normals: sign(side) * row c of S
+    cf = torch.tensor(face // 2, device=dev)
+    sg = torch.tensor(np.where(face % 2 == 0, -1.0, 1.0), **t64)
+    n_f = sg[:, None, None] * S_f[torch.arange(nf, device=dev), cf]        # (nf, ne, 3)
+    # interpolated interior primitives at the flux points
+    wsr = w_s.reshape(5, q, q, q, ne)                                      # (v, jz, jy, jx, e)
+    wint = torch.empty((5, nf, ne), **t64)
+    lm = torch.tensor(B["lm"], **t64)
+    lp = torch.tensor(B["lp"], **t64)
+    for f in range(nf):
+        c, s = face[f] // 2, face[f] % 2
+        ijk = fpts[f]
+        wl = lm if s == 0 else lp
+        sel = [ijk[2], ijk[1], ijk[0]]                                     # (jz, jy, jx)
+        sel[2 - c] = slice(None)
+        line = wsr[:, sel[0], sel[1], sel[2]]                              # (5, q, ne)
+        wint[:, f] = (wl[None, :, None] * line).sum(1)
+    dw_f = w_f - wint
+    Finv = _euler_rows_t(q_f, gamma)                                       # (5, nf, ne, 3)
+    nFinv = (Finv * n_f[None]).sum(-1)
+    f32 = lambda t: t.to(torch.float32).contiguous()
+    return {
+        "dims": tuple(dims), "order": order, "gamma": gamma,
+        "w_s": f32(w_s.permute(1, 0, 2)), "q_s": f32(q_s.permute(1, 0, 2)),
+        "S_s": f32(S_s), "detJ_s": f32(det_s),
+        "q_f": f32(q_f.permute(1, 0, 2)), "S_f": f32(S_f), "detJ_f": f32(det_f),
+        "n_f": f32(n_f[:, None]), "dw_f": f32(dw_f.permute(1, 0, 2)),
+        "nFinv_f": f32(nFinv.permute(1, 0, 2)),
+    }
