@@ -46,12 +46,14 @@ def parse_args():
     p.add_argument("--no-extra", action="store_true", help="skip the baseline/extra measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--workload", choices=["add", "tgv", "batched", "precision", "fdiv", "sweep",
-                                          "gather"],
+                                          "gather", "fr"],
                    default="add",
                    help="add: the headline line; the others print their own JSON line")
     p.add_argument("--tgv-elements", type=int, default=96)
     p.add_argument("--fdiv-elements", type=int, default=96,
                    help="elements per axis of the flux-divergence mesh")
+    p.add_argument("--fr-elements", type=int, default=96,
+                   help="elements per axis of the mesh of the FR steps 5-11")
     return p.parse_args()
 
 
@@ -777,6 +779,110 @@ def run_fdiv(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fr(args):
+    """Steps 5-11 of Table fr_nse (Sec. 4) of the flux-reconstruction
+    Navier-Stokes right-hand side on a periodic E^3 hex mesh of degree 3, with
+    the gradient, metric, normal and flux tensors as compressed rows and, as
+    the baseline, as FP32 rows: the chain 5 -> 6 -> 7 -> 8, 9 -> 10 -> 11, each
+    step timed on its own.  The bytes each step moves per element come from
+    the memory model of Table mem_usage (fr_memory); its prediction is the
+    byte ratio, the measurement the time ratio."""
+    import torch
+
+    from paper_2003_02633_gb300 import fr_memory, ivc, synth
+    dev = torch.device("cuda", 0)
+    fmt = ivc.default_format()
+    E = args.fr_elements
+    order = 3
+    dims = (E, E, E)
+    ne = E ** 3
+    c = synth.fr_case(dims, order, device=dev)
+    basis = ivc.fr_basis(synth.fr_basis(order))
+    gas = ivc.fr_gas()
+    ns, nf = (order + 1) ** 3, 6 * (order + 1) ** 2
+
+    def rows32(t):
+        return t.permute(3, 0, 1, 2).contiguous()
+
+    def words(t):
+        return ivc.compress(fmt, t.reshape(-1, 3)).reshape(t.shape[:3])
+
+    geo = {}
+    for k in ("S_s", "S_f", "n_f"):
+        geo[k + "32"], geo[k + "w"] = rows32(c[k]), words(c[k])
+        del c[k]
+    w_s, q_s, det_s = c["w_s"], c["q_s"], c["detJ_s"]
+    dw_f, q_f, det_f, nFi = c["dw_f"], c["q_f"], c["detJ_f"], c["nFinv_f"]
+    D = torch.from_numpy(synth.fr_hex_operator(order, 2.0)).to(dev)   # reference element
+    f32 = dict(grad=torch.empty((3, ns, 5, ne), device=dev), gradc=torch.empty((3, ns, 5, ne),
+               device=dev), gradf=torch.empty((3, nf, 5, ne), device=dev),
+               F=torch.empty((3, ns, 5, ne), device=dev))
+    cw = {k: torch.empty((ns if k != "gradf" else nf, 5, ne), dtype=torch.int64, device=dev)
+          for k in ("grad", "gradc", "gradf", "F")}
+    out = {k: (torch.empty((nf, 5, ne), device=dev), torch.empty((nf, 5, ne), device=dev))
+           for k in ("nF", "Fc")}
+    out["div"] = (torch.empty((ns, 5, ne), device=dev), torch.empty((ns, 5, ne), device=dev))
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+
+    def chain(f, R, G, k):          # k: 0 FP32, 1 compressed
+        g = "32" if k == 0 else "w"
+        return {
+            5: lambda: ivc.fr_gradient(f, basis, w_s, out=R["grad"], stream=s),
+            6: lambda: ivc.fr_correct_gradient(f, basis, R["grad"], dw_f, out=R["gradc"],
+                                               stream=s),
+            7: lambda: ivc.fr_interp_rows(f, basis, R["gradc"], out=R["gradf"], stream=s),
+            8: lambda: ivc.fr_common_viscous_flux(f, order, gas, dims, R["gradf"], G["n_f" + g],
+                                                  G["S_f" + g], det_f, q_f, nFi,
+                                                  out=out["nF"][k], stream=s),
+            9: lambda: ivc.fr_flux(f, order, gas, q_s, R["gradc"], G["S_s" + g], det_s,
+                                   out=R["F"], stream=s),
+            10: (lambda: ivc.f32_flux_divergence(R["F"], D, out=out["div"][k], stream=s))
+            if f is None else
+            (lambda: ivc.flux_divergence(f, R["F"], D, out=out["div"][k], stream=s)),
+            11: lambda: ivc.fr_flux_correction(f, basis, R["F"], out["nF"][k], out=out["Fc"][k],
+                                               stream=s),
+        }
+
+    runs = (chain(None, f32, geo, 0), chain(fmt, cw, geo, 1))
+    order_steps = (5, 6, 7, 8, 9, 10, 11)
+    for r in runs:
+        for st in order_steps:
+            r[st]()
+    torch.cuda.synchronize()
+    ivc.flux_divergence_check()
+    steps, warmup = max(3, min(args.steps, 20)), max(3, min(args.warmup, 5))
+    hbm_gbs, _ = measured_peaks()
+    rows = []
+    tot = [0.0, 0.0]
+    byt = [0, 0]
+    for st in order_steps:
+        ms = [_time_ms(r[st], steps, warmup, stream)[0] for r in runs]
+        b32 = fr_memory.step_bytes(order, st)
+        bc = fr_memory.step_bytes(order, st, compressed=True)
+        for i in range(2):
+            tot[i] += ms[i]
+        byt[0] += b32
+        byt[1] += bc
+        rows.append({"step": st, "fp32_ms": round(ms[0], 4), "compressed_ms": round(ms[1], 4),
+                     "time_ratio": round(ms[1] / ms[0], 4), "gamma_bytes": round(bc / b32, 4),
+                     "fp32_gbs": round(b32 * ne / (ms[0] * 1e-3) / 1e9, 1),
+                     "compressed_gbs": round(bc * ne / (ms[1] * 1e-3) / 1e9, 1)})
+    ivc.flux_divergence_check()
+    t_all, g_all = fr_memory.totals(order)
+    line = {"workload": "fr_steps_5_11", "elements": ne, "order": order, "nvars": 5,
+            "steps": steps, "per_step": rows,
+            "steps_5_11": {"fp32_ms": round(tot[0], 4), "compressed_ms": round(tot[1], 4),
+                           "time_ratio": round(tot[1] / tot[0], 4),
+                           "predicted_ratio_bytes": round(byt[1] / byt[0], 4)},
+            "table_mem_usage_k3": {"total_kib": round(t_all, 2), "gamma": round(g_all, 4),
+                                   "predicted_gain": round(1 - g_all, 4)},
+            "hbm_peak_gbs": hbm_gbs,
+            "data": "synthetic: Taylor-Green state (Sec. 4.2) with a 5% smooth perturbation "
+                    "on a periodic hex mesh deformed by 0.1 sin-products, degree 3"}
+    print(json.dumps(line), flush=True)
+
+
 def run_sweep(args):
     """The paper's size sweep of Sec. 5 (Fig. speedup): compressed add against
     the FP32x3 add (AoS) for N = 2^10 ... 2^28 on one GPU.  The L2 is flushed
@@ -881,6 +987,8 @@ def main():
         run_sweep(args)
     elif args.workload == "gather":
         run_gather(args)
+    elif args.workload == "fr":
+        run_fr(args)
     else:
         run_ivc(args)
 

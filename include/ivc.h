@@ -300,6 +300,116 @@ ivc_status ivc_add_host(const ivc_format *fmt, const uint64_t *a, const uint64_t
                         uint64_t *c, int64_t n, void *workspace, size_t ws_bytes,
                         ivc_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Flux-reconstruction steps 5-11 of Table fr_nse (Sec. 4) with compressed
+ * tensor rows.  Higher-dimensional terms (gradients, metric terms, normals,
+ * fluxes) are compressed row by row (Eq. eulerF): every row is one 3-vector,
+ * one 64-bit word.  Step 10 is ivc_flux_divergence.  Each step has an FP32
+ * counterpart (ivc_f32_fr_*) with the same arithmetic on uncompressed rows.
+ *
+ * Elements are hexahedra of degree k = order (1..3) with q = k + 1
+ * Gauss-Legendre points per axis: ns = q^3 solution points, j = (jz q + jy) q
+ * + jx, and nf = 6 q^2 flux points, f = (2 c + s) q^2 + b q + a on the face of
+ * axis c (0, 1, 2 = x, y, z) and side s (0 at xi_c = -1, 1 at +1), with a, b
+ * the indices along the other two axes in increasing order.
+ *
+ * Layout (element index e fastest; one leading dimension ld >= ne for every
+ * array of a call): a scalar of point k and variable v at [(k nv + v) ld + e];
+ * a compressed row at the same index of a uint64_t array; an FP32 row with
+ * component c at [((c npts + k) nv + v) ld + e] (npts = ns or nf).  Metric
+ * rows use nv = 3 (the rows of S = |J| J^-1, J = dx/dxi), normals nv = 1.
+ * Entries with e >= ne are neither read nor written.  The caller owns every
+ * buffer (device memory); unless stated, inputs and outputs must not overlap.
+ * Arithmetic is FP32 on the decoded rows; compressed outputs are encoded as
+ * ivc_compress does.
+ * Errors: IVC_ERR_ARG (order outside 1..3, nvars outside 1..5, ne < 0,
+ * ld < ne, NULL pointers with ne > 0, mesh dims whose product is not ne),
+ * IVC_ERR_ALIGN (words not 8-byte, floats not 4-byte aligned), IVC_ERR_FORMAT.
+ * ------------------------------------------------------------------------ */
+
+/* The one-dimensional basis on the q Gauss-Legendre points xi_i of [-1, 1]. */
+typedef struct {
+  int order;          /* k, 1..3 */
+  float dm[16];       /* dm[i * q + a] = l_a'(xi_i), derivative of basis function a */
+  float lm[4], lp[4]; /* l_a(-1), l_a(+1): interpolation to the ends */
+  float gl[4], gr[4]; /* g_L'(xi_i), g_R'(xi_i): derivatives of the correction functions */
+} ivc_fr_basis;
+
+/* Constant-property gas: ratio of specific heats, dynamic viscosity, Prandtl
+ * number (heat flux kappa grad T = mu gamma / ((gamma - 1) Pr) grad(p / rho)). */
+typedef struct {
+  float gamma, mu, prandtl;
+} ivc_fr_gas;
+
+/* Step 5: grad(k, v) = sum_a dm[k_c][a] w(point k with k_c = a, v) along each
+ * axis c: the reference-space gradient rows of the nvars scalars w (the
+ * primitives) at the solution points. */
+ivc_status ivc_fr_gradient(const ivc_format *fmt, const ivc_fr_basis *basis, const float *w,
+                           int64_t ne, int64_t ld, int nvars, uint64_t *grad,
+                           ivc_stream_t stream);
+ivc_status ivc_f32_fr_gradient(const ivc_fr_basis *basis, const float *w, int64_t ne,
+                               int64_t ld, int nvars, float *grad, ivc_stream_t stream);
+
+/* Step 6: grad_c(k, v)_c = grad(k, v)_c + gl[k_c] dw(f_L, v) + gr[k_c] dw(f_R, v)
+ * with f_L, f_R the flux points of the two faces of axis c on the line of k
+ * and dw the interface jumps (w^I - w^f) at the flux points (scalars, nf
+ * points).  grad_c may equal grad (in place). */
+ivc_status ivc_fr_correct_gradient(const ivc_format *fmt, const ivc_fr_basis *basis,
+                                   const uint64_t *grad, const float *dw, int64_t ne, int64_t ld,
+                                   int nvars, uint64_t *grad_c, ivc_stream_t stream);
+ivc_status ivc_f32_fr_correct_gradient(const ivc_fr_basis *basis, const float *grad,
+                                       const float *dw, int64_t ne, int64_t ld, int nvars,
+                                       float *grad_c, ivc_stream_t stream);
+
+/* Step 7: rows at the flux points, rows_f(f, v) = sum_i l_i(-1 or +1) rows(point
+ * i along the face's axis on the line of f, v). */
+ivc_status ivc_fr_interp_rows(const ivc_format *fmt, const ivc_fr_basis *basis,
+                              const uint64_t *rows, int64_t ne, int64_t ld, int nvars,
+                              uint64_t *rows_f, ivc_stream_t stream);
+ivc_status ivc_f32_fr_interp_rows(const ivc_fr_basis *basis, const float *rows, int64_t ne,
+                                  int64_t ld, int nvars, float *rows_f, ivc_stream_t stream);
+
+/* Step 8: out(f, v) = nFinv(f, v) - n(f) . F_vis^I(f, v) at every flux point
+ * of every element of a periodic dims[0] x dims[1] x dims[2] mesh (ne = the
+ * product, e = (ez dims[1] + ey) dims[0] + ex), with the BR1 common viscous
+ * flux F_vis^I = (F_vis(this side) + F_vis(partner)) / 2; the partner is the
+ * point with the same (a, b) on the facing face of the neighbouring element.
+ * F_vis is the compressible Navier-Stokes viscous flux (Stokes hypothesis) of
+ * the conserved q_f (5 scalars) and the physical gradient (S^T grad_f) / |J|
+ * of the primitives (rho, u, v, w, p) from their reference gradient rows
+ * grad_f (5 rows), the metric rows S_f (3 rows) and detJ_f = |J|.  nrm: one
+ * row per flux point, this side's scaled normal.  nvars = 5. */
+ivc_status ivc_fr_common_viscous_flux(const ivc_format *fmt, int order, const ivc_fr_gas *gas,
+                                      const int dims[3], const uint64_t *grad_f,
+                                      const uint64_t *nrm, const uint64_t *S_f,
+                                      const float *detJ_f, const float *q_f, const float *nFinv,
+                                      int64_t ld, float *out, ivc_stream_t stream);
+ivc_status ivc_f32_fr_common_viscous_flux(int order, const ivc_fr_gas *gas, const int dims[3],
+                                          const float *grad_f, const float *nrm,
+                                          const float *S_f, const float *detJ_f,
+                                          const float *q_f, const float *nFinv, int64_t ld,
+                                          float *out, ivc_stream_t stream);
+
+/* Step 9: the reference flux rows F(k, v) = S (F_inv - F_vis) at the solution
+ * points from the conserved q_s (5 scalars), the primitives' reference
+ * gradient rows grad (5 rows), the metric rows S_s (3 rows) and detJ_s; the
+ * rows of F_inv are those of Eq. eulerF.  nvars = 5. */
+ivc_status ivc_fr_flux(const ivc_format *fmt, int order, const ivc_fr_gas *gas, const float *q_s,
+                       const uint64_t *grad, const uint64_t *S_s, const float *detJ_s,
+                       int64_t ne, int64_t ld, uint64_t *F, ivc_stream_t stream);
+ivc_status ivc_f32_fr_flux(int order, const ivc_fr_gas *gas, const float *q_s, const float *grad,
+                           const float *S_s, const float *detJ_s, int64_t ne, int64_t ld,
+                           float *F, ivc_stream_t stream);
+
+/* Step 11: Fc(f, v) = nF(f, v) - sign(s) (row F interpolated to f)_c: the
+ * interface flux minus the interior normal flux (scalars at the flux points). */
+ivc_status ivc_fr_flux_correction(const ivc_format *fmt, const ivc_fr_basis *basis,
+                                  const uint64_t *F, const float *nF, int64_t ne, int64_t ld,
+                                  int nvars, float *Fc, ivc_stream_t stream);
+ivc_status ivc_f32_fr_flux_correction(const ivc_fr_basis *basis, const float *F, const float *nF,
+                                      int64_t ne, int64_t ld, int nvars, float *Fc,
+                                      ivc_stream_t stream);
+
 /* Frees the cached per-format tables on the current device. */
 ivc_status ivc_release_tables(void);
 

@@ -3,6 +3,7 @@
 // launch-shape tuner.  Kernels live in ivc_ops.cu and ivc_baseline.cu.
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -541,6 +542,206 @@ ivc_status ivc_f32_flux_divergence(const float *F, int64_t ld, int ns, int nvars
   DevFormat none{};
   return cuda_status(launch_flux_div(IVC_MAP_UNIFORM, false, true, none, F, ld, ns, nvars, ne, D,
                                      div, ld_out, stream));
+}
+
+// ------------------------------------------------- flux reconstruction (5-11)
+
+namespace {
+
+// Validates the common arguments of an FR step and fills the call; `fmt`
+// NULL selects FP32 rows.  Returns IVC_OK with call->ne == 0 for empty work.
+ivc_status fr_prepare(int step, const ivc_format *fmt, const ivc_fr_basis *basis, int order,
+                      const ivc_fr_gas *gas, int64_t ne, int64_t ld, int nvars,
+                      std::initializer_list<const void *> ins, void *out, FrCall *call) {
+  *call = FrCall{};
+  call->step = step;
+  call->f32 = fmt == nullptr;
+  if (fmt) {
+    ivc_status st = ivc::format_fields(fmt, &call->F, &call->map);
+    if (st != IVC_OK) return st;
+  }
+  if (basis) {
+    call->basis = *basis;
+    order = basis->order;
+  } else {
+    call->basis.order = order;
+  }
+  if (order < 1 || order > 3 || nvars < 1 || nvars > 5 || ne < 0) return IVC_ERR_ARG;
+  if (gas) call->gas = *gas;
+  call->ne = ne;
+  call->ld = ld;
+  call->nv = nvars;
+  if (ne == 0) return IVC_OK;
+  if (ld < ne || !out) return IVC_ERR_ARG;
+  const void *p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int i = 0;
+  for (const void *x : ins) {
+    if (!x) return IVC_ERR_ARG;
+    if (!aligned(x, 4)) return IVC_ERR_ALIGN;
+    p[i++] = x;
+  }
+  if (!aligned(out, 4)) return IVC_ERR_ALIGN;
+  call->in0 = p[0];
+  call->in1 = p[1];
+  call->in2 = p[2];
+  call->in3 = p[3];
+  call->in4 = p[4];
+  call->in5 = p[5];
+  call->out = out;
+  return IVC_OK;
+}
+
+// Word arrays must be 8-byte aligned.
+ivc_status words_aligned(std::initializer_list<const void *> ws) {
+  for (const void *w : ws)
+    if (w && !aligned(w, 8)) return IVC_ERR_ALIGN;
+  return IVC_OK;
+}
+
+ivc_status fr_run(FrCall &call, const ivc_format *fmt, ivc_stream_t stream) {
+  if (call.ne == 0) return IVC_OK;
+  if (fmt) {
+    ivc_status st = make_devformat(fmt, &call.F, &call.map);
+    if (st != IVC_OK) return st;
+  }
+  return cuda_status(launch_fr(call, stream));
+}
+
+}  // namespace
+
+ivc_status ivc_fr_gradient(const ivc_format *fmt, const ivc_fr_basis *basis, const float *w,
+                           int64_t ne, int64_t ld, int nvars, uint64_t *grad,
+                           ivc_stream_t stream) {
+  if (!fmt || !basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(5, fmt, basis, 0, nullptr, ne, ld, nvars, {w}, grad, &c);
+  if (st == IVC_OK && ne > 0) st = words_aligned({grad});
+  return st != IVC_OK ? st : fr_run(c, fmt, stream);
+}
+
+ivc_status ivc_f32_fr_gradient(const ivc_fr_basis *basis, const float *w, int64_t ne,
+                               int64_t ld, int nvars, float *grad, ivc_stream_t stream) {
+  if (!basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(5, nullptr, basis, 0, nullptr, ne, ld, nvars, {w}, grad, &c);
+  return st != IVC_OK ? st : fr_run(c, nullptr, stream);
+}
+
+ivc_status ivc_fr_correct_gradient(const ivc_format *fmt, const ivc_fr_basis *basis,
+                                   const uint64_t *grad, const float *dw, int64_t ne, int64_t ld,
+                                   int nvars, uint64_t *grad_c, ivc_stream_t stream) {
+  if (!fmt || !basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(6, fmt, basis, 0, nullptr, ne, ld, nvars, {grad, dw}, grad_c, &c);
+  if (st == IVC_OK && ne > 0) st = words_aligned({grad, grad_c});
+  return st != IVC_OK ? st : fr_run(c, fmt, stream);
+}
+
+ivc_status ivc_f32_fr_correct_gradient(const ivc_fr_basis *basis, const float *grad,
+                                       const float *dw, int64_t ne, int64_t ld, int nvars,
+                                       float *grad_c, ivc_stream_t stream) {
+  if (!basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(6, nullptr, basis, 0, nullptr, ne, ld, nvars, {grad, dw}, grad_c,
+                             &c);
+  return st != IVC_OK ? st : fr_run(c, nullptr, stream);
+}
+
+ivc_status ivc_fr_interp_rows(const ivc_format *fmt, const ivc_fr_basis *basis,
+                              const uint64_t *rows, int64_t ne, int64_t ld, int nvars,
+                              uint64_t *rows_f, ivc_stream_t stream) {
+  if (!fmt || !basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(7, fmt, basis, 0, nullptr, ne, ld, nvars, {rows}, rows_f, &c);
+  if (st == IVC_OK && ne > 0) st = words_aligned({rows, rows_f});
+  return st != IVC_OK ? st : fr_run(c, fmt, stream);
+}
+
+ivc_status ivc_f32_fr_interp_rows(const ivc_fr_basis *basis, const float *rows, int64_t ne,
+                                  int64_t ld, int nvars, float *rows_f, ivc_stream_t stream) {
+  if (!basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(7, nullptr, basis, 0, nullptr, ne, ld, nvars, {rows}, rows_f, &c);
+  return st != IVC_OK ? st : fr_run(c, nullptr, stream);
+}
+
+namespace {
+
+ivc_status fr_common_viscous(const ivc_format *fmt, int order, const ivc_fr_gas *gas,
+                             const int dims[3], const void *grad_f, const void *nrm,
+                             const void *S_f, const float *detJ_f, const float *q_f,
+                             const float *nFinv, int64_t ld, float *out, ivc_stream_t stream) {
+  if (!gas || !dims) return IVC_ERR_ARG;
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return IVC_ERR_ARG;
+  const int64_t ne = (int64_t)dims[0] * dims[1] * dims[2];
+  FrCall c;
+  ivc_status st = fr_prepare(8, fmt, nullptr, order, gas, ne, ld, 5,
+                             {grad_f, nrm, S_f, detJ_f, q_f, nFinv}, out, &c);
+  if (st == IVC_OK && fmt) st = words_aligned({grad_f, nrm, S_f});
+  if (st != IVC_OK) return st;
+  for (int i = 0; i < 3; ++i) c.dims[i] = dims[i];
+  return fr_run(c, fmt, stream);
+}
+
+}  // namespace
+
+ivc_status ivc_fr_common_viscous_flux(const ivc_format *fmt, int order, const ivc_fr_gas *gas,
+                                      const int dims[3], const uint64_t *grad_f,
+                                      const uint64_t *nrm, const uint64_t *S_f,
+                                      const float *detJ_f, const float *q_f, const float *nFinv,
+                                      int64_t ld, float *out, ivc_stream_t stream) {
+  if (!fmt) return IVC_ERR_ARG;
+  return fr_common_viscous(fmt, order, gas, dims, grad_f, nrm, S_f, detJ_f, q_f, nFinv, ld, out,
+                           stream);
+}
+
+ivc_status ivc_f32_fr_common_viscous_flux(int order, const ivc_fr_gas *gas, const int dims[3],
+                                          const float *grad_f, const float *nrm,
+                                          const float *S_f, const float *detJ_f,
+                                          const float *q_f, const float *nFinv, int64_t ld,
+                                          float *out, ivc_stream_t stream) {
+  return fr_common_viscous(nullptr, order, gas, dims, grad_f, nrm, S_f, detJ_f, q_f, nFinv, ld,
+                           out, stream);
+}
+
+ivc_status ivc_fr_flux(const ivc_format *fmt, int order, const ivc_fr_gas *gas, const float *q_s,
+                       const uint64_t *grad, const uint64_t *S_s, const float *detJ_s,
+                       int64_t ne, int64_t ld, uint64_t *F, ivc_stream_t stream) {
+  if (!fmt || !gas) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(9, fmt, nullptr, order, gas, ne, ld, 5, {q_s, grad, S_s, detJ_s}, F,
+                             &c);
+  if (st == IVC_OK && ne > 0) st = words_aligned({grad, S_s, F});
+  return st != IVC_OK ? st : fr_run(c, fmt, stream);
+}
+
+ivc_status ivc_f32_fr_flux(int order, const ivc_fr_gas *gas, const float *q_s, const float *grad,
+                           const float *S_s, const float *detJ_s, int64_t ne, int64_t ld,
+                           float *F, ivc_stream_t stream) {
+  if (!gas) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(9, nullptr, nullptr, order, gas, ne, ld, 5,
+                             {q_s, grad, S_s, detJ_s}, F, &c);
+  return st != IVC_OK ? st : fr_run(c, nullptr, stream);
+}
+
+ivc_status ivc_fr_flux_correction(const ivc_format *fmt, const ivc_fr_basis *basis,
+                                  const uint64_t *F, const float *nF, int64_t ne, int64_t ld,
+                                  int nvars, float *Fc, ivc_stream_t stream) {
+  if (!fmt || !basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(11, fmt, basis, 0, nullptr, ne, ld, nvars, {F, nF}, Fc, &c);
+  if (st == IVC_OK && ne > 0) st = words_aligned({F});
+  return st != IVC_OK ? st : fr_run(c, fmt, stream);
+}
+
+ivc_status ivc_f32_fr_flux_correction(const ivc_fr_basis *basis, const float *F, const float *nF,
+                                      int64_t ne, int64_t ld, int nvars, float *Fc,
+                                      ivc_stream_t stream) {
+  if (!basis) return IVC_ERR_ARG;
+  FrCall c;
+  ivc_status st = fr_prepare(11, nullptr, basis, 0, nullptr, ne, ld, nvars, {F, nF}, Fc, &c);
+  return st != IVC_OK ? st : fr_run(c, nullptr, stream);
 }
 
 // ------------------------------------------------------------------ batched

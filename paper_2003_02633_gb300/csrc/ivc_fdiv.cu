@@ -21,6 +21,7 @@
 // degree 3; it runs on the FP32 pipes because its operands carry 24-bit
 // significands and the result is held to an FP32 summation bound (a TF32 or
 // BF16 tensor-core product would round the decoded flux to 11 or 8 bits).
+#include "ivc_decode_poles.cuh"
 #include "ivc_internal.h"
 
 namespace ivc {
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(Wb + q * 4);
           if (MODE == FD_FAST) {
-            fast::decode2_full<fast::GeoPrimary>(w.x, w.y, F, tab_t, tab_p, vx, vy, vz);
+            fast::decode2_poles<fast::GeoPrimary>(w.x, w.y, F, tab_t, tab_p, vx, vy, vz);
           } else {
             const float3 a = decode_word<MAP>(w.x, F, tab_t, tab_p);
             const float3 c3 = decode_word<MAP>(w.y, F, tab_t, tab_p);

@@ -1,6 +1,7 @@
 // Random-access decompression (the unstructured access of Sec. 1): the
 // decoded vectors at an index list, AoS FP32 out.  Kernels of their own file
 // so that the streaming kernels' sources stay as profiled.
+#include "ivc_decode_poles.cuh"
 #include "ivc_internal.h"
 
 namespace ivc {
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) k_gather_fast(const __grid_constant__ Dev
     const uint64_t w0 = ok0 ? __ldg(w + jj.x) : 0ull;
     const uint64_t w1 = ok1 ? __ldg(w + jj.y) : 0ull;
     float2 X, Y, Z;
-    fast::decode2_full<G>(w0, w1, F, tab_t, tab_p, X, Y, Z);
+    fast::decode2_poles<G>(w0, w1, F, tab_t, tab_p, X, Y, Z);
     const float qn = __int_as_float(0x7fc00000);
     if (!ok0) X.x = Y.x = Z.x = qn;
     if (!ok1) X.y = Y.y = Z.y = qn;

@@ -104,6 +104,24 @@ cudaError_t launch_flux_div(int map, bool fast_path, bool f32, const DevFormat &
                             const void *src, int64_t ld, int ns, int nv, int64_t ne,
                             const float *D, float *div, int64_t ld_out, cudaStream_t st);
 
+// One flux-reconstruction step (5-9, 11) on compressed rows of format (map, F)
+// or, with f32, on FP32 rows; in0..in5 and out in the step's argument order
+// of the C ABI.  The launcher sizes its own grid.
+struct FrCall {
+  int step;
+  bool f32;
+  int map;
+  DevFormat F;
+  ivc_fr_basis basis;
+  ivc_fr_gas gas;
+  int dims[3];
+  int64_t ne, ld;
+  int nv;
+  const void *in0, *in1, *in2, *in3, *in4, *in5;
+  void *out;
+};
+cudaError_t launch_fr(const FrCall &call, cudaStream_t st);
+
 // Reads and clears the flux-divergence kernels' device status word (1: a
 // bounded wait between the decoding and the accumulating warps ran out).
 cudaError_t flux_div_status(int *status);

@@ -53,11 +53,24 @@ class ivc_launch_config(ctypes.Structure):
                 ("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
+class ivc_fr_basis(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("dm", ctypes.c_float * 16),
+                ("lm", ctypes.c_float * 4), ("lp", ctypes.c_float * 4),
+                ("gl", ctypes.c_float * 4), ("gr", ctypes.c_float * 4)]
+
+
+class ivc_fr_gas(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_float), ("mu", ctypes.c_float), ("prandtl", ctypes.c_float)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _F = ctypes.c_float
 _I = ctypes.c_int
 _FMT = ctypes.POINTER(ivc_format)
+_BAS = ctypes.POINTER(ivc_fr_basis)
+_GAS = ctypes.POINTER(ivc_fr_gas)
+_DIMS = ctypes.POINTER(ctypes.c_int)
 _SIGS = {
     "ivc_format_default": [_FMT],
     "ivc_format_validate": [_FMT],
@@ -90,6 +103,18 @@ _SIGS = {
     "ivc_flux_divergence_check": [],
     "ivc_gather_decompress": [_FMT, _P, _I64, _P, _I64, _P, _P],
     "ivc_f32_gather": [_I, _P, _I64, _I64, _P, _I64, _P, _P],
+    "ivc_fr_gradient": [_FMT, _BAS, _P, _I64, _I64, _I, _P, _P],
+    "ivc_f32_fr_gradient": [_BAS, _P, _I64, _I64, _I, _P, _P],
+    "ivc_fr_correct_gradient": [_FMT, _BAS, _P, _P, _I64, _I64, _I, _P, _P],
+    "ivc_f32_fr_correct_gradient": [_BAS, _P, _P, _I64, _I64, _I, _P, _P],
+    "ivc_fr_interp_rows": [_FMT, _BAS, _P, _I64, _I64, _I, _P, _P],
+    "ivc_f32_fr_interp_rows": [_BAS, _P, _I64, _I64, _I, _P, _P],
+    "ivc_fr_common_viscous_flux": [_FMT, _I, _GAS, _DIMS, _P, _P, _P, _P, _P, _P, _I64, _P, _P],
+    "ivc_f32_fr_common_viscous_flux": [_I, _GAS, _DIMS, _P, _P, _P, _P, _P, _P, _I64, _P, _P],
+    "ivc_fr_flux": [_FMT, _I, _GAS, _P, _P, _P, _P, _I64, _I64, _P, _P],
+    "ivc_f32_fr_flux": [_I, _GAS, _P, _P, _P, _P, _I64, _I64, _P, _P],
+    "ivc_fr_flux_correction": [_FMT, _BAS, _P, _P, _I64, _I64, _I, _P, _P],
+    "ivc_f32_fr_flux_correction": [_BAS, _P, _P, _I64, _I64, _I, _P, _P],
 }
 EXPORTS = sorted(list(_SIGS) + ["ivc_status_string", "ivc_version"])
 
@@ -236,6 +261,119 @@ def f32_flux_divergence(F, D, ne=None, out=None, stream=None):
     _chk(load().ivc_f32_flux_divergence(_ptr(F), ld, ns, nv, ne, _ptr(D), _ptr(out),
                                         out.shape[2], _stream(stream)),
          "ivc_f32_flux_divergence")
+    return out
+
+
+# ------------------------------------------- flux reconstruction, steps 5-11
+# Every wrapper takes ``fmt``: an ivc_format for compressed rows (int64 word
+# tensors of shape (npts, nrows, ld)), or None for the FP32 baseline (float32
+# tensors of shape (3, npts, nrows, ld)).  Scalars are float32 (npts, nv, ld).
+# ``ne`` (default ld) elements are processed.
+
+
+def fr_basis(b: dict) -> ivc_fr_basis:
+    """The C struct of a one-dimensional basis given as a dict with ``order``
+    and the arrays ``dm`` (q x q, dm[i, a] = l_a'(xi_i)), ``lm``, ``lp``, ``gl``,
+    ``gr`` (rounded to FP32)."""
+    q = int(b["order"]) + 1
+    out = ivc_fr_basis()
+    out.order = int(b["order"])
+    dm = [float(v) for row in b["dm"] for v in row]
+    for i in range(q * q):
+        out.dm[i] = dm[i]
+    for name in ("lm", "lp", "gl", "gr"):
+        arr = getattr(out, name)
+        for i in range(q):
+            arr[i] = float(b[name][i])
+    return out
+
+
+def fr_gas(gamma: float = 1.4, mu: float = 1.0 / 1600.0, prandtl: float = 0.72) -> ivc_fr_gas:
+    return ivc_fr_gas(gamma, mu, prandtl)
+
+
+def _rows_like(fmt, npts, nrows, ld, device):
+    import torch
+    if fmt is None:
+        return torch.empty((3, npts, nrows, ld), dtype=torch.float32, device=device)
+    return torch.empty((npts, nrows, ld), dtype=torch.int64, device=device)
+
+
+def _fr(name, fmt, *args):
+    lib = load()
+    if fmt is None:
+        _chk(getattr(lib, "ivc_f32_" + name)(*args), "ivc_f32_" + name)
+    else:
+        _chk(getattr(lib, "ivc_" + name)(ctypes.byref(fmt), *args), "ivc_" + name)
+
+
+def fr_gradient(fmt, basis, w, ne=None, out=None, stream=None):
+    """Step 5: gradient rows of the scalars w (ns, nv, ld) at the solution points."""
+    ns, nv, ld = w.shape
+    ne = ld if ne is None else int(ne)
+    if out is None:
+        out = _rows_like(fmt, ns, nv, ld, w.device)
+    _fr("fr_gradient", fmt, ctypes.byref(basis), _ptr(w), ne, ld, nv, _ptr(out), _stream(stream))
+    return out
+
+
+def fr_correct_gradient(fmt, basis, grad, dw, ne=None, out=None, stream=None):
+    """Step 6: gradient rows plus the lifted jumps dw (nf, nv, ld); out may be grad."""
+    nf, nv, ld = dw.shape
+    ns = grad.shape[-3]
+    ne = ld if ne is None else int(ne)
+    if out is None:
+        out = _rows_like(fmt, ns, nv, ld, grad.device)
+    _fr("fr_correct_gradient", fmt, ctypes.byref(basis), _ptr(grad), _ptr(dw), ne, ld, nv,
+        _ptr(out), _stream(stream))
+    return out
+
+
+def fr_interp_rows(fmt, basis, rows, ne=None, out=None, stream=None):
+    """Step 7: rows (ns, nv, ld) interpolated to the flux points (nf, nv, ld)."""
+    ns, nv, ld = rows.shape[-3:]
+    q = round(ns ** (1.0 / 3.0))
+    ne = ld if ne is None else int(ne)
+    if out is None:
+        out = _rows_like(fmt, 6 * q * q, nv, ld, rows.device)
+    _fr("fr_interp_rows", fmt, ctypes.byref(basis), _ptr(rows), ne, ld, nv, _ptr(out),
+        _stream(stream))
+    return out
+
+
+def fr_common_viscous_flux(fmt, order, gas, dims, grad_f, nrm, S_f, detJ_f, q_f, nFinv,
+                           out=None, stream=None):
+    """Step 8: n.(F_inv - F_vis^I) (nf, 5, ld) on the periodic dims mesh."""
+    import torch
+    nf, _, ld = q_f.shape
+    if out is None:
+        out = torch.empty((nf, 5, ld), dtype=torch.float32, device=q_f.device)
+    d = (ctypes.c_int * 3)(*[int(x) for x in dims])
+    _fr("fr_common_viscous_flux", fmt, int(order), ctypes.byref(gas), d, _ptr(grad_f), _ptr(nrm),
+        _ptr(S_f), _ptr(detJ_f), _ptr(q_f), _ptr(nFinv), ld, _ptr(out), _stream(stream))
+    return out
+
+
+def fr_flux(fmt, order, gas, q_s, grad, S_s, detJ_s, ne=None, out=None, stream=None):
+    """Step 9: reference flux rows S (F_inv - F_vis) (ns, 5, ld)."""
+    ns, _, ld = q_s.shape
+    ne = ld if ne is None else int(ne)
+    if out is None:
+        out = _rows_like(fmt, ns, 5, ld, q_s.device)
+    _fr("fr_flux", fmt, int(order), ctypes.byref(gas), _ptr(q_s), _ptr(grad), _ptr(S_s),
+        _ptr(detJ_s), ne, ld, _ptr(out), _stream(stream))
+    return out
+
+
+def fr_flux_correction(fmt, basis, F, nF, ne=None, out=None, stream=None):
+    """Step 11: nF (nf, nv, ld) minus the interior normal flux of rows F."""
+    import torch
+    nf, nv, ld = nF.shape
+    ne = ld if ne is None else int(ne)
+    if out is None:
+        out = torch.empty((nf, nv, ld), dtype=torch.float32, device=nF.device)
+    _fr("fr_flux_correction", fmt, ctypes.byref(basis), _ptr(F), _ptr(nF), ne, ld, nv,
+        _ptr(out), _stream(stream))
     return out
 
 

@@ -490,11 +490,13 @@ def fr_case(dims=(4, 4, 4), order: int = 3, deform: float = 0.1, perturb: float 
         dM = [[one, A * cy * sz, A * sy * cz],
               [A * sz * cx, one, A * cz * sx],
               [A * cx * sy, A * sx * cy, one]]
-        J = torch.stack([torch.stack([dM[i][j] * (0.5 * hs[j]) for j in range(3)], -1)
-                         for i in range(3)], -2)                            # (npts, ne, 3, 3)
-        det = torch.linalg.det(J)
-        S = det[..., None, None] * torch.linalg.inv(J)                     # rows of |J| J^-1
-        return X, S.permute(0, 2, 1, 3).contiguous(), det
+        # columns of J = dx/dxi; S = |J| J^-1 is the adjugate, whose row r is
+        # the cross product of columns r + 1 and r + 2
+        cols = [torch.stack([dM[i][j] * (0.5 * hs[j]) for i in range(3)], -1) for j in range(3)]
+        S = torch.stack([torch.linalg.cross(cols[(r + 1) % 3], cols[(r + 2) % 3], dim=-1)
+                         for r in range(3)], 1)                             # (npts, 3, ne, 3)
+        det = (cols[0] * S[:, 0]).sum(-1)
+        return X, S.contiguous(), det
 
     def flow(X):
         x, y, z = X

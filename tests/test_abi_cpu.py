@@ -117,3 +117,50 @@ def test_argument_errors_before_device_work(lib):
     assert ws.value >= 4 * 48
     assert lib.ivc_launch_plan(None, None) == ivc.IVC_ERR_ARG
     assert lib.ivc_plan_destroy(None) == ivc.IVC_ERR_ARG
+
+
+def test_fr_argument_errors_before_device_work(lib):
+    from paper_2003_02633_gb300 import synth
+    f = ivc.default_format()
+    bad = ivc.make_format(exp_bits=9)
+    B = ivc.fr_basis(synth.fr_basis(3))
+    B0 = ivc.fr_basis(synth.fr_basis(3))
+    B0.order = 4                                   # degree outside 1..3
+    gas = ivc.fr_gas()
+    ref = ctypes.byref
+    g = lib.ivc_fr_gradient
+    assert g(ref(f), ref(B), None, 0, 0, 5, None, None) == ivc.IVC_OK      # empty
+    assert g(ref(f), ref(B), None, -1, 0, 5, None, None) == ivc.IVC_ERR_ARG
+    assert g(ref(f), ref(B), None, 4, 2, 5, None, None) == ivc.IVC_ERR_ARG  # ld < ne
+    assert g(ref(f), ref(B), None, 4, 4, 6, None, None) == ivc.IVC_ERR_ARG  # nvars
+    assert g(ref(f), ref(B0), None, 0, 0, 5, None, None) == ivc.IVC_ERR_ARG
+    assert g(ref(f), None, None, 0, 0, 5, None, None) == ivc.IVC_ERR_ARG
+    assert g(ref(bad), ref(B), None, 4, 4, 5, None, None) == ivc.IVC_ERR_FORMAT
+    assert g(ref(f), ref(B), None, 4, 4, 5, None, None) == ivc.IVC_ERR_ARG  # NULL w
+    buf = (ctypes.c_uint64 * 8)()
+    a8 = ctypes.addressof(buf)
+    assert g(ref(f), ref(B), a8, 4, 4, 5, a8 + 4, None) == ivc.IVC_ERR_ALIGN
+    assert lib.ivc_f32_fr_gradient(ref(B), None, 4, 4, 5, None, None) == ivc.IVC_ERR_ARG
+    cg = lib.ivc_fr_correct_gradient
+    assert cg(ref(f), ref(B), a8, None, 4, 4, 5, a8, None) == ivc.IVC_ERR_ARG
+    assert cg(ref(f), ref(B), a8 + 4, a8, 4, 4, 5, a8, None) == ivc.IVC_ERR_ALIGN
+    ir = lib.ivc_fr_interp_rows
+    assert ir(ref(f), ref(B), None, 0, 0, 1, None, None) == ivc.IVC_OK
+    assert ir(ref(f), ref(B), a8, 4, 4, 0, a8, None) == ivc.IVC_ERR_ARG
+    dims = (ctypes.c_int * 3)(2, 2, 2)
+    zero = (ctypes.c_int * 3)(2, 0, 2)
+    cv = lib.ivc_fr_common_viscous_flux
+    assert cv(ref(f), 3, ref(gas), zero, a8, a8, a8, a8, a8, a8, 8, a8, None) == ivc.IVC_ERR_ARG
+    assert cv(ref(f), 3, ref(gas), dims, a8, a8, a8, a8, a8, a8, 4, a8, None) == ivc.IVC_ERR_ARG
+    assert cv(ref(f), 0, ref(gas), dims, a8, a8, a8, a8, a8, a8, 8, a8, None) == ivc.IVC_ERR_ARG
+    assert cv(ref(f), 3, None, dims, a8, a8, a8, a8, a8, a8, 8, a8, None) == ivc.IVC_ERR_ARG
+    assert cv(ref(f), 3, ref(gas), dims, a8, None, a8, a8, a8, a8, 8, a8, None) == \
+        ivc.IVC_ERR_ARG
+    fl = lib.ivc_fr_flux
+    assert fl(ref(f), 3, ref(gas), None, None, None, None, 0, 0, None, None) == ivc.IVC_OK
+    assert fl(ref(f), 3, ref(gas), a8, a8, a8, None, 4, 4, a8, None) == ivc.IVC_ERR_ARG
+    assert fl(ref(f), 3, ref(gas), a8, a8 + 4, a8, a8, 4, 4, a8, None) == ivc.IVC_ERR_ALIGN
+    fc = lib.ivc_fr_flux_correction
+    assert fc(ref(bad), ref(B), a8, a8, 4, 4, 5, a8, None) == ivc.IVC_ERR_FORMAT
+    assert fc(ref(f), ref(B), a8, a8, 4, 3, 5, a8, None) == ivc.IVC_ERR_ARG
+    assert lib.ivc_f32_fr_flux_correction(ref(B), a8, a8, 4, 4, 0, a8, None) == ivc.IVC_ERR_ARG

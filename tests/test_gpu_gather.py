@@ -76,3 +76,29 @@ def test_f32_gather(layout):
     ok = (idx >= 0) & (idx < nsrc)
     assert np.array_equal(got[ok], x[idx[ok]])
     assert np.all(np.isnan(got[~ok]))
+
+
+@pytest.mark.parametrize("fname", ["primary", "fracsplit"])
+def test_gather_pole_words_exact(fname):
+    # words at the poles (n_phi = 0 or n_phi_max) with any n_theta and any
+    # magnitude decode to exactly (+0, +0, +-r^), settled in the fast kernel
+    fo, fg = formats(fname)
+    N, M = O.nmax(fo)
+    rng = np.random.default_rng(21)
+    n = 4096
+    E = rng.integers(0, 128, n).astype(np.uint64)          # includes 0 and non-finite 127
+    m = rng.integers(0, 1 << 22, n).astype(np.uint64)
+    nt = rng.integers(0, N + 1, n).astype(np.uint64)
+    npv = np.where(rng.random(n) < 0.5, 0, M).astype(np.uint64)
+    if fo.map == 2:
+        low = npv * np.uint64(N + 1) + nt
+    else:
+        low = (npv << np.uint64(18)) | nt
+    w = (E << np.uint64(57)) | (m << np.uint64(35)) | low
+    Wd = torch.from_numpy(w.view(np.int64)).to(DEV)
+    idx = torch.arange(n, dtype=torch.int64, device=DEV)
+    got = ivc.gather_decompress(fg, Wd, idx).cpu().numpy()
+    want = O.decompress(fo, w)
+    fin = np.isfinite(want).all(1)
+    assert np.array_equal(got[fin].view(np.uint32), want[fin].view(np.uint32))
+    check_decoded(got, want, f"gather poles {fname}")
