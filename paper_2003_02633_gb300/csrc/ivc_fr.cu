@@ -599,8 +599,11 @@ __device__ __forceinline__ void side_viscous(const C &codec, const float *qf,
 }
 
 // Step 8: n . (F_inv - F^I_vis) at every flux point of every element, with
-// F^I_vis the mean of this side's and the partner side's viscous fluxes
-// (BR1); the partner is the matching point of the facing element.
+// F^I_vis the mean of the two sides' viscous fluxes (BR1).  Each interface is
+// evaluated once: the thread of flux point f on the + face of axis c of
+// element e also writes the matching point f - q^2 on the - face of the
+// neighbour e' across it (a bijection on a periodic mesh, so every output has
+// one writer), and each side's rows are decoded once.
 template <class C>
 __global__ void __launch_bounds__(kThreads) k_fr_commonvis(
     const __grid_constant__ DevFormat F, FrGasDev gas, FrSmem L, int q, int Ex, int Ey, int Ez,
@@ -609,38 +612,55 @@ __global__ void __launch_bounds__(kThreads) k_fr_commonvis(
     int64_t ne, int64_t ld, float *out) {
   extern __shared__ __align__(16) unsigned char smem[];
   C codec = CodecOf<C>::make(F, smem, L);
-  const int nf = 6 * q * q;
+  const int nf = 6 * q * q, nplus = 3 * q * q;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ntiles = (ne + kTile - 1) / kTile;
-  const int64_t items = ntiles * nf;
+  const int64_t items = ntiles * nplus;
   const int64_t cs5 = (int64_t)nf * 5 * ld, cs3 = (int64_t)nf * 3 * ld, cs1 = (int64_t)nf * ld;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
   for (int64_t it = gw; it < items; it += nw) {
-    const int64_t e0 = (it / nf) * kTile;
-    const int f = (int)(it % nf);
+    const int64_t e0 = (it / nplus) * kTile;
+    const int j = (int)(it % nplus);                // + face point: axis c, in-face index
+    const int c = j / (q * q);
+    const int f = (2 * c + 1) * q * q + j % (q * q), fo = f - q * q;
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
-    const int face = f / (q * q), c = face >> 1, s = face & 1;
-    const int fo = s ? f - q * q : f + q * q;
-    const int64_t pa = va ? neighbour(ea, c, s, Ex, Ey, Ez) : 0;
-    const int64_t pb = vb ? neighbour(eb, c, s, Ex, Ey, Ez) : 0;
+    const int64_t pa = va ? neighbour(ea, c, 1, Ex, Ey, Ez) : 0;
+    const int64_t pb = vb ? neighbour(eb, c, 1, Ex, Ey, Ez) : 0;
     float Fa[4][3], Fb[4][3], Pa[4][3], Pb[4][3];
     side_viscous(codec, qf, G, S, detJ, f, ea, eb, va, vb, ld, cs5, cs3, gas, Fa, Fb);
     side_viscous(codec, qf, G, S, detJ, fo, pa, pb, va, vb, ld, cs5, cs3, gas, Pa, Pb);
-    float2 nx, ny, nz;
+    float2 nx, ny, nz, mx, my, mz;
     codec.load2(nrm, (int64_t)f * ld + ea, (int64_t)f * ld + eb, va, vb, cs1, nx, ny, nz);
+    codec.load2(nrm, (int64_t)fo * ld + pa, (int64_t)fo * ld + pb, va, vb, cs1, mx, my, mz);
     for (int v = 0; v < 5; ++v) {
-      const int64_t idx = ((int64_t)f * 5 + v) * ld;
+      const int64_t idx = ((int64_t)f * 5 + v) * ld, ido = ((int64_t)fo * 5 + v) * ld;
       if (v == 0) {
-        if (va) out[idx + ea] = __ldg(nFinv + idx + ea);
-        if (vb) out[idx + eb] = __ldg(nFinv + idx + eb);
+        if (va) {
+          out[idx + ea] = __ldg(nFinv + idx + ea);
+          out[ido + pa] = __ldg(nFinv + ido + pa);
+        }
+        if (vb) {
+          out[idx + eb] = __ldg(nFinv + idx + eb);
+          out[ido + pb] = __ldg(nFinv + ido + pb);
+        }
         continue;
       }
       const float *fa = Fa[v - 1], *fb = Fb[v - 1], *ga = Pa[v - 1], *gb = Pb[v - 1];
-      const float da = fmaf(nz.x, fa[2] + ga[2], fmaf(ny.x, fa[1] + ga[1], nx.x * (fa[0] + ga[0])));
-      const float db = fmaf(nz.y, fb[2] + gb[2], fmaf(ny.y, fb[1] + gb[1], nx.y * (fb[0] + gb[0])));
-      if (va) out[idx + ea] = fmaf(-0.5f, da, __ldg(nFinv + idx + ea));
-      if (vb) out[idx + eb] = fmaf(-0.5f, db, __ldg(nFinv + idx + eb));
+      const float sa0 = fa[0] + ga[0], sa1 = fa[1] + ga[1], sa2 = fa[2] + ga[2];
+      const float sb0 = fb[0] + gb[0], sb1 = fb[1] + gb[1], sb2 = fb[2] + gb[2];
+      if (va) {
+        out[idx + ea] = fmaf(-0.5f, fmaf(nz.x, sa2, fmaf(ny.x, sa1, nx.x * sa0)),
+                             __ldg(nFinv + idx + ea));
+        out[ido + pa] = fmaf(-0.5f, fmaf(mz.x, sa2, fmaf(my.x, sa1, mx.x * sa0)),
+                             __ldg(nFinv + ido + pa));
+      }
+      if (vb) {
+        out[idx + eb] = fmaf(-0.5f, fmaf(nz.y, sb2, fmaf(ny.y, sb1, nx.y * sb0)),
+                             __ldg(nFinv + idx + eb));
+        out[ido + pb] = fmaf(-0.5f, fmaf(mz.y, sb2, fmaf(my.y, sb1, mx.y * sb0)),
+                             __ldg(nFinv + ido + pb));
+      }
     }
   }
   codec.finish();
@@ -675,11 +695,13 @@ cudaError_t launch_shape(K kernel, size_t smem, int64_t blocks_needed, int *grid
 
 size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Shared-memory plan of a codec and a staging buffer of `stage` bytes.
+// Shared-memory plan of a codec and a staging buffer of `stage` bytes; the
+// per-warp queues only for kernels that encode.
 template <class C>
-FrSmem smem_plan(const DevFormat &F, int map, size_t stage, size_t *total) {
+FrSmem smem_plan(const DevFormat &F, int map, size_t stage, size_t *total, bool encodes = true) {
   size_t tab = C::kWords ? align16(table_smem_bytes(F, map)) : 0;
-  size_t queue = C::kQueue ? (size_t)kWarps * fast::kQueueCap * sizeof(fast::PendItem) : 0;
+  size_t queue = (C::kQueue && encodes)
+                     ? (size_t)kWarps * fast::kQueueCap * sizeof(fast::PendItem) : 0;
   FrSmem L;
   L.off_queue = (int)tab;
   L.off_stage = (int)(tab + align16(queue));
@@ -758,7 +780,7 @@ cudaError_t launch_fr(const FrCall &a, cudaStream_t st) {
         break;
       }
       case 11: {
-        const FrSmem L = smem_plan<C>(a.F, a.map, (size_t)ns * 3 * kTile * 4, &smem);
+        const FrSmem L = smem_plan<C>(a.F, a.map, (size_t)ns * 3 * kTile * 4, &smem, false);
         if ((e = launch_shape(k_fr_fcorr<C>, smem, ntiles * a.nv, &grid)) != cudaSuccess)
           return e;
         k_fr_fcorr<C><<<grid, kThreads, smem, st>>>(a.F, B, L, (const T *)a.in0,
@@ -778,8 +800,8 @@ cudaError_t launch_fr(const FrCall &a, cudaStream_t st) {
         break;
       }
       case 8: {
-        const FrSmem L = smem_plan<C>(a.F, a.map, 0, &smem);
-        const int64_t warps = ntiles * nf;
+        const FrSmem L = smem_plan<C>(a.F, a.map, 0, &smem, false);
+        const int64_t warps = ntiles * (nf / 2);
         if ((e = launch_shape(k_fr_commonvis<C>, smem, (warps + kWarps - 1) / kWarps, &grid)) !=
             cudaSuccess)
           return e;
