@@ -92,11 +92,18 @@ struct FastRows {
   const TabEntry *tab_t, *tab_p;
   fast::WarpQueue wq;
 
-  __device__ void load2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t,
+  struct Raw {
+    uint64_t w0, w1;
+  };
+  __device__ Raw fetch2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t) const {
+    return Raw{v0 ? __ldg(src + i0) : 0ull, v1 ? __ldg(src + i1) : 0ull};
+  }
+  __device__ void decode_raw(const Raw &r, float2 &X, float2 &Y, float2 &Z) const {
+    fast::decode2_poles<G>(r.w0, r.w1, F, tab_t, tab_p, X, Y, Z);
+  }
+  __device__ void load2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t cs,
                         float2 &X, float2 &Y, float2 &Z) const {
-    const uint64_t w0 = v0 ? __ldg(src + i0) : 0ull;
-    const uint64_t w1 = v1 ? __ldg(src + i1) : 0ull;
-    fast::decode2_poles<G>(w0, w1, F, tab_t, tab_p, X, Y, Z);
+    decode_raw(fetch2(src, i0, i1, v0, v1, cs), X, Y, Z);
   }
   __device__ void store2(T *dst, int64_t i0, int64_t i1, bool v0, bool v1, int64_t, float2 X,
                          float2 Y, float2 Z) {
@@ -119,14 +126,22 @@ struct GenericRows {
   const DevFormat &F;
   const TabEntry *tab_t, *tab_p;
 
-  __device__ void load2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t,
-                        float2 &X, float2 &Y, float2 &Z) const {
-    float3 a = make_float3(0.0f, 0.0f, 0.0f), b = a;
-    if (v0) a = decode_word<MAP>(__ldg(src + i0), F, tab_t, tab_p);
-    if (v1) b = decode_word<MAP>(__ldg(src + i1), F, tab_t, tab_p);
+  struct Raw {
+    uint64_t w0, w1;  // 0 (the zero vector) for an absent element
+  };
+  __device__ Raw fetch2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t) const {
+    return Raw{v0 ? __ldg(src + i0) : 0ull, v1 ? __ldg(src + i1) : 0ull};
+  }
+  __device__ void decode_raw(const Raw &r, float2 &X, float2 &Y, float2 &Z) const {
+    const float3 a = decode_word<MAP>(r.w0, F, tab_t, tab_p);
+    const float3 b = decode_word<MAP>(r.w1, F, tab_t, tab_p);
     X = make_float2(a.x, b.x);
     Y = make_float2(a.y, b.y);
     Z = make_float2(a.z, b.z);
+  }
+  __device__ void load2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t cs,
+                        float2 &X, float2 &Y, float2 &Z) const {
+    decode_raw(fetch2(src, i0, i1, v0, v1, cs), X, Y, Z);
   }
   __device__ void store2(T *dst, int64_t i0, int64_t i1, bool v0, bool v1, int64_t, float2 X,
                          float2 Y, float2 Z) {
@@ -144,11 +159,24 @@ struct F32Rows {
   static constexpr bool kQueue = false;
   static constexpr int MAP = MAP_UNIFORM;
 
+  struct Raw {
+    float2 x, y, z;
+  };
+  __device__ Raw fetch2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1,
+                        int64_t cs) const {
+    return Raw{make_float2(v0 ? __ldg(src + i0) : 0.0f, v1 ? __ldg(src + i1) : 0.0f),
+               make_float2(v0 ? __ldg(src + i0 + cs) : 0.0f, v1 ? __ldg(src + i1 + cs) : 0.0f),
+               make_float2(v0 ? __ldg(src + i0 + 2 * cs) : 0.0f,
+                           v1 ? __ldg(src + i1 + 2 * cs) : 0.0f)};
+  }
+  __device__ void decode_raw(const Raw &r, float2 &X, float2 &Y, float2 &Z) const {
+    X = r.x;
+    Y = r.y;
+    Z = r.z;
+  }
   __device__ void load2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t cs,
                         float2 &X, float2 &Y, float2 &Z) const {
-    X = make_float2(v0 ? __ldg(src + i0) : 0.0f, v1 ? __ldg(src + i1) : 0.0f);
-    Y = make_float2(v0 ? __ldg(src + i0 + cs) : 0.0f, v1 ? __ldg(src + i1 + cs) : 0.0f);
-    Z = make_float2(v0 ? __ldg(src + i0 + 2 * cs) : 0.0f, v1 ? __ldg(src + i1 + 2 * cs) : 0.0f);
+    decode_raw(fetch2(src, i0, i1, v0, v1, cs), X, Y, Z);
   }
   __device__ void store2(T *dst, int64_t i0, int64_t i1, bool v0, bool v1, int64_t cs, float2 X,
                          float2 Y, float2 Z) {
@@ -498,6 +526,32 @@ __device__ __forceinline__ void point_flux(const float qv[5], const float G[5][3
       out[v][r] = fmaf(S[r][2], Fp[v][2], fmaf(S[r][1], Fp[v][1], S[r][0] * Fp[v][0]));
 }
 
+// The inputs of the pointwise physics at one point for two elements: every
+// load of the point is issued before the first decode, so the decodes wait
+// for memory once.
+template <class C>
+struct PointIn {
+  float qa[5], qb[5], ja, jb;
+  typename C::Raw g[5], s[3];
+
+  __device__ void fetch(const C &codec, const float *qsrc, const typename C::T *G,
+                        const typename C::T *S, const float *detJ, int k, int64_t ea, int64_t eb,
+                        bool va, bool vb, int64_t ld, int64_t cs5, int64_t cs3) {
+    for (int v = 0; v < 5; ++v) {
+      const int64_t idx = ((int64_t)k * 5 + v) * ld;
+      qa[v] = va ? __ldg(qsrc + idx + ea) : 1.0f;
+      qb[v] = vb ? __ldg(qsrc + idx + eb) : 1.0f;
+      g[v] = codec.fetch2(G, idx + ea, idx + eb, va, vb, cs5);
+    }
+    for (int r = 0; r < 3; ++r) {
+      const int64_t idx = ((int64_t)k * 3 + r) * ld;
+      s[r] = codec.fetch2(S, idx + ea, idx + eb, va, vb, cs3);
+    }
+    ja = va ? __ldg(detJ + (int64_t)k * ld + ea) : 1.0f;
+    jb = vb ? __ldg(detJ + (int64_t)k * ld + eb) : 1.0f;
+  }
+};
+
 // Splits a pair of rows into per-element arrays.
 __device__ __forceinline__ void unpair(float2 X, float2 Y, float2 Z, float a[3], float b[3]) {
   a[0] = X.x; a[1] = Y.x; a[2] = Z.x;
@@ -526,26 +580,22 @@ __global__ void __launch_bounds__(kThreads) k_fr_flux(const __grid_constant__ De
     const int k = (int)(it % ns);
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
-    float qa[5], qb[5], Ga[5][3], Gb[5][3], Sa[3][3], Sb[3][3];
+    PointIn<C> in;
+    in.fetch(codec, qs, G, S, detJ, k, ea, eb, va, vb, ld, cs5, cs3);
+    float Ga[5][3], Gb[5][3], Sa[3][3], Sb[3][3];
     for (int v = 0; v < 5; ++v) {
-      const int64_t idx = ((int64_t)k * 5 + v) * ld;
-      qa[v] = va ? __ldg(qs + idx + ea) : 1.0f;
-      qb[v] = vb ? __ldg(qs + idx + eb) : 1.0f;
       float2 X, Y, Z;
-      codec.load2(G, idx + ea, idx + eb, va, vb, cs5, X, Y, Z);
+      codec.decode_raw(in.g[v], X, Y, Z);
       unpair(X, Y, Z, Ga[v], Gb[v]);
     }
     for (int r = 0; r < 3; ++r) {
-      const int64_t idx = ((int64_t)k * 3 + r) * ld;
       float2 X, Y, Z;
-      codec.load2(S, idx + ea, idx + eb, va, vb, cs3, X, Y, Z);
+      codec.decode_raw(in.s[r], X, Y, Z);
       unpair(X, Y, Z, Sa[r], Sb[r]);
     }
-    const float ja = va ? __ldg(detJ + (int64_t)k * ld + ea) : 1.0f;
-    const float jb = vb ? __ldg(detJ + (int64_t)k * ld + eb) : 1.0f;
     float Fa[5][3], Fb[5][3];
-    point_flux(qa, Ga, Sa, ja, gas, Fa);
-    point_flux(qb, Gb, Sb, jb, gas, Fb);
+    point_flux(in.qa, Ga, Sa, in.ja, gas, Fa);
+    point_flux(in.qb, Gb, Sb, in.jb, gas, Fb);
     for (int v = 0; v < 5; ++v) {
       const int64_t idx = ((int64_t)k * 5 + v) * ld;
       codec.store2(Fs, idx + ea, idx + eb, va, vb, cs5, make_float2(Fa[v][0], Fb[v][0]),
@@ -566,36 +616,27 @@ __device__ __forceinline__ int64_t neighbour(int64_t e, int c, int s, int Ex, in
   return (iz * Ey + iy) * Ex + ix;
 }
 
-// Viscous flux rows at one flux point of one side.
+// Viscous flux rows of one side from its fetched inputs.
 template <class C>
-__device__ __forceinline__ void side_viscous(const C &codec, const float *qf,
-                                             const typename C::T *G, const typename C::T *S,
-                                             const float *detJ, int f, int64_t ea, int64_t eb,
-                                             bool va, bool vb, int64_t ld, int64_t cs5,
-                                             int64_t cs3, const FrGasDev &gas, float Fa[4][3],
-                                             float Fb[4][3]) {
-  float qa[5], qb[5], Ga[5][3], Gb[5][3], Sa[3][3], Sb[3][3];
+__device__ __forceinline__ void side_viscous_from(const C &codec, const PointIn<C> &in,
+                                                  const FrGasDev &gas, float Fa[4][3],
+                                                  float Fb[4][3]) {
+  float Ga[5][3], Gb[5][3], Sa[3][3], Sb[3][3];
   for (int v = 0; v < 5; ++v) {
-    const int64_t idx = ((int64_t)f * 5 + v) * ld;
-    qa[v] = va ? __ldg(qf + idx + ea) : 1.0f;
-    qb[v] = vb ? __ldg(qf + idx + eb) : 1.0f;
     float2 X, Y, Z;
-    codec.load2(G, idx + ea, idx + eb, va, vb, cs5, X, Y, Z);
+    codec.decode_raw(in.g[v], X, Y, Z);
     unpair(X, Y, Z, Ga[v], Gb[v]);
   }
   for (int r = 0; r < 3; ++r) {
-    const int64_t idx = ((int64_t)f * 3 + r) * ld;
     float2 X, Y, Z;
-    codec.load2(S, idx + ea, idx + eb, va, vb, cs3, X, Y, Z);
+    codec.decode_raw(in.s[r], X, Y, Z);
     unpair(X, Y, Z, Sa[r], Sb[r]);
   }
-  const float ja = va ? __ldg(detJ + (int64_t)f * ld + ea) : 1.0f;
-  const float jb = vb ? __ldg(detJ + (int64_t)f * ld + eb) : 1.0f;
   float gx[5][3];
-  physical_gradient(Ga, Sa, ja, gx);
-  viscous_rows(qa, gx, gas, Fa);
-  physical_gradient(Gb, Sb, jb, gx);
-  viscous_rows(qb, gx, gas, Fb);
+  physical_gradient(Ga, Sa, in.ja, gx);
+  viscous_rows(in.qa, gx, gas, Fa);
+  physical_gradient(Gb, Sb, in.jb, gx);
+  viscous_rows(in.qb, gx, gas, Fb);
 }
 
 // Step 8: n . (F_inv - F^I_vis) at every flux point of every element, with
@@ -628,8 +669,11 @@ __global__ void __launch_bounds__(kThreads) k_fr_commonvis(
     const int64_t pa = va ? neighbour(ea, c, 1, Ex, Ey, Ez) : 0;
     const int64_t pb = vb ? neighbour(eb, c, 1, Ex, Ey, Ez) : 0;
     float Fa[4][3], Fb[4][3], Pa[4][3], Pb[4][3];
-    side_viscous(codec, qf, G, S, detJ, f, ea, eb, va, vb, ld, cs5, cs3, gas, Fa, Fb);
-    side_viscous(codec, qf, G, S, detJ, fo, pa, pb, va, vb, ld, cs5, cs3, gas, Pa, Pb);
+    PointIn<C> in0, in1;                            // both sides' loads in flight at once
+    in0.fetch(codec, qf, G, S, detJ, f, ea, eb, va, vb, ld, cs5, cs3);
+    in1.fetch(codec, qf, G, S, detJ, fo, pa, pb, va, vb, ld, cs5, cs3);
+    side_viscous_from(codec, in0, gas, Fa, Fb);
+    side_viscous_from(codec, in1, gas, Pa, Pb);
     float2 nx, ny, nz, mx, my, mz;
     codec.load2(nrm, (int64_t)f * ld + ea, (int64_t)f * ld + eb, va, vb, cs1, nx, ny, nz);
     codec.load2(nrm, (int64_t)fo * ld + pa, (int64_t)fo * ld + pb, va, vb, cs1, mx, my, mz);
