@@ -333,13 +333,25 @@ __global__ void __launch_bounds__(kThreads) k_fr_correct(const __grid_constant__
       sd[f * kTile + lane] = va ? __ldg(row + ea) : 0.0f;
       sd[f * kTile + lane + 32] = vb ? __ldg(row + eb) : 0.0f;
     }
+    // the gradient rows are fetched one point ahead (the first before the barrier)
+    typename C::Raw cur{};
+    if (warp < ns) {
+      const int64_t idx = ((int64_t)warp * nv + v) * ld;
+      cur = codec.fetch2(G, idx + ea, idx + eb, va, vb, cs);
+    }
     __syncthreads();
     for (int k = warp; k < ns; k += kWarps) {
       int ijk[3];
       point_ijk(k, q, ijk);
       const int64_t idx = ((int64_t)k * nv + v) * ld;
+      typename C::Raw nxt = cur;
+      if (k + kWarps < ns) {
+        const int64_t idn = ((int64_t)(k + kWarps) * nv + v) * ld;
+        nxt = codec.fetch2(G, idn + ea, idn + eb, va, vb, cs);
+      }
       float2 g[3];
-      codec.load2(G, idx + ea, idx + eb, va, vb, cs, g[0], g[1], g[2]);
+      codec.decode_raw(cur, g[0], g[1], g[2]);
+      cur = nxt;
       for (int c = 0; c < 3; ++c) {
         const int fl = flux_point(c, 0, ijk, q), fr = fl + q * q;
         const float wl = B.gl[ijk[c]], wr = B.gr[ijk[c]];
@@ -357,25 +369,56 @@ __global__ void __launch_bounds__(kThreads) k_fr_correct(const __grid_constant__
 // ------------------------------------------------------------ steps 7, 11
 
 // Stages the tile's rows of variable v at the ns solution points, decoded, as
-// [k][c][64] FP32.
-template <class C>
+// [k][c][64] FP32.  AHEAD issues all of a warp's loads before its first decode
+// (faster where the registers it takes do not cost occupancy: the compressed
+// interpolation; slower for the correction kernel and for FP32 rows, measured).
+template <bool AHEAD, class C>
 __device__ __forceinline__ void stage_rows(const C &codec, const typename C::T *X, float *sx,
                                            int ns, int nv, int v, int64_t ld, int64_t e0,
                                            int64_t ne, int64_t cs) {
+  constexpr int kPer = (kMaxQ * kMaxQ * kMaxQ + kWarps - 1) / kWarps;  // points per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ea = e0 + lane, eb = e0 + lane + 32;
   const bool va = ea < ne, vb = eb < ne;
-  for (int k = warp; k < ns; k += kWarps) {
-    const int64_t idx = ((int64_t)k * nv + v) * ld;
-    float2 X0, Y0, Z0;
-    codec.load2(X, idx + ea, idx + eb, va, vb, cs, X0, Y0, Z0);
-    float *s = sx + k * 3 * kTile;
-    s[lane] = X0.x;
-    s[lane + 32] = X0.y;
-    s[kTile + lane] = Y0.x;
-    s[kTile + lane + 32] = Y0.y;
-    s[2 * kTile + lane] = Z0.x;
-    s[2 * kTile + lane + 32] = Z0.y;
+  if (!AHEAD) {
+    for (int k = warp; k < ns; k += kWarps) {
+      const int64_t idx = ((int64_t)k * nv + v) * ld;
+      float2 X0, Y0, Z0;
+      codec.load2(X, idx + ea, idx + eb, va, vb, cs, X0, Y0, Z0);
+      float *s = sx + k * 3 * kTile;
+      s[lane] = X0.x;
+      s[lane + 32] = X0.y;
+      s[kTile + lane] = Y0.x;
+      s[kTile + lane + 32] = Y0.y;
+      s[2 * kTile + lane] = Z0.x;
+      s[2 * kTile + lane + 32] = Z0.y;
+    }
+    return;
+  }
+  // all of this warp's loads first, then the decodes
+  typename C::Raw raw[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int k = warp + i * kWarps;
+    if (k < ns) {
+      const int64_t idx = ((int64_t)k * nv + v) * ld;
+      raw[i] = codec.fetch2(X, idx + ea, idx + eb, va, vb, cs);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int k = warp + i * kWarps;
+    if (k < ns) {
+      float2 X0, Y0, Z0;
+      codec.decode_raw(raw[i], X0, Y0, Z0);
+      float *s = sx + k * 3 * kTile;
+      s[lane] = X0.x;
+      s[lane + 32] = X0.y;
+      s[kTile + lane] = Y0.x;
+      s[kTile + lane + 32] = Y0.y;
+      s[2 * kTile + lane] = Z0.x;
+      s[2 * kTile + lane + 32] = Z0.y;
+    }
   }
 }
 
@@ -418,7 +461,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_interp(const __grid_constant__ 
     const int v = (int)(it % nv);
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
-    stage_rows(codec, X, sx, ns, nv, v, ld, e0, ne, cs_in);
+    stage_rows<C::kWords>(codec, X, sx, ns, nv, v, ld, e0, ne, cs_in);
     __syncthreads();
     for (int f = warp; f < nf; f += kWarps) {
       const float2 x = line_value(sx, B, f, 0, lane);
@@ -453,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_fcorr(const __grid_constant__ D
     const int v = (int)(it % nv);
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
-    stage_rows(codec, Fs, sx, ns, nv, v, ld, e0, ne, cs_in);
+    stage_rows<false>(codec, Fs, sx, ns, nv, v, ld, e0, ne, cs_in);
     __syncthreads();
     for (int f = warp; f < nf; f += kWarps) {
       const int face = f / (q * q);
