@@ -87,6 +87,7 @@ struct FastRows {
   using T = uint64_t;
   static constexpr bool kWords = true;
   static constexpr bool kQueue = true;
+  static constexpr int kInterfaceBlocks = 2;  // resident blocks asked of step 8 (registers)
   static constexpr int MAP = G::MAP;
   const DevFormat &F;
   const TabEntry *tab_t, *tab_p;
@@ -122,6 +123,7 @@ struct GenericRows {
   using T = uint64_t;
   static constexpr bool kWords = true;
   static constexpr bool kQueue = false;
+  static constexpr int kInterfaceBlocks = 1;
   static constexpr int MAP = MAP_;
   const DevFormat &F;
   const TabEntry *tab_t, *tab_p;
@@ -157,6 +159,7 @@ struct F32Rows {
   using T = float;
   static constexpr bool kWords = false;
   static constexpr bool kQueue = false;
+  static constexpr int kInterfaceBlocks = 1;
   static constexpr int MAP = MAP_UNIFORM;
 
   struct Raw {
@@ -689,7 +692,7 @@ __device__ __forceinline__ void side_viscous_from(const C &codec, const PointIn<
 // neighbour e' across it (a bijection on a periodic mesh, so every output has
 // one writer), and each side's rows are decoded once.
 template <class C>
-__global__ void __launch_bounds__(kThreads) k_fr_commonvis(
+__global__ void __launch_bounds__(kThreads, C::kInterfaceBlocks) k_fr_commonvis(
     const __grid_constant__ DevFormat F, FrGasDev gas, FrSmem L, int q, int Ex, int Ey, int Ez,
     const typename C::T *G, const typename C::T *nrm, const typename C::T *S,
     const float *__restrict__ detJ, const float *__restrict__ qf, const float *__restrict__ nFinv,

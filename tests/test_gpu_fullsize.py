@@ -24,6 +24,7 @@ from paper_2003_02633_gb300 import ivc, synth  # noqa: E402
 from parity_util import check_decoded, check_words  # noqa: E402
 
 DEV = "cuda:0"
+FR_E = 96          # elements per axis of the FR mesh (the benchmark's)
 
 
 def test_add_full_size_sampled():
@@ -91,3 +92,91 @@ def test_gather_full_size_sampled():
     j = idx[s]
     words = w[j].cpu().numpy().view(np.uint64)
     check_decoded(out[s].cpu().numpy(), O.decompress(O.PRIMARY, words), "gather (N = 2^28)")
+
+
+def _fr_sample_words(fmt_o, rows_dev, sel_t, what):
+    """GPU-compressed words of synth rows, with the sampled elements' words
+    checked against the oracle's compression of the same rows; as in the add
+    above, the oracle then works on those (checked) words."""
+    fmt = ivc.default_format()
+    W = ivc.compress(fmt, rows_dev.reshape(-1, 3)).reshape(rows_dev.shape[:3])
+    host = rows_dev[:, :, sel_t].cpu().numpy()                       # (npts, nr, ns, 3)
+    wo = O.compress(fmt_o, host.reshape(-1, 3)).reshape(host.shape[:3])
+    wg = W[:, :, sel_t].cpu().numpy().view(np.uint64)
+    check_words(fmt_o, host.reshape(-1, 3), wg.reshape(-1), wo.reshape(-1), what)
+    return W, wg
+
+
+def test_fr_interp_and_interface_full_size_sampled():
+    # steps 7 and 8 of Table fr_nse on the 96^3 degree-3 mesh of the benchmark
+    # (synth.fr_case, same launch shapes), 24 sampled elements against the oracle
+    from oracle import fr as R
+    E, order = FR_E, 3
+    dims = (E, E, E)
+    dev = torch.device(DEV)
+    fo = O.PRIMARY
+    fmt = ivc.default_format()
+    c = synth.fr_case(dims, order, device=dev)
+    ne = E ** 3
+    ns, nf = 64, 96
+    bas = synth.fr_basis(order)
+    B32 = {k: (np.asarray(v, np.float32).astype(np.float64) if k in ("dm", "lm", "lp", "gl", "gr")
+               else v) for k, v in bas.items()}
+    rng = np.random.default_rng(8)
+    sel = np.sort(rng.choice(ne, size=24, replace=False))
+    st = torch.from_numpy(sel).to(dev)
+    # step 7 on gradient-like rows (the benchmark's vector distribution)
+    X = synth.device_vectors(ns * 5 * ne, 41, dev).reshape(ns, 5, ne, 3)
+    Wx, wx = _fr_sample_words(fo, X, st, "step 7 inputs")
+    del X
+    out = ivc.fr_interp_rows(fmt, ivc.fr_basis(bas), Wx)
+    got = O.decompress(fo, out[:, :, st].cpu().numpy().view(np.uint64).reshape(-1)).reshape(
+        nf, 5, sel.size, 3).astype(np.float64)
+    Xv = O.decompress(fo, wx.reshape(-1)).reshape(ns, 5, sel.size, 3).astype(np.float64)
+    ref = R.interp_rows(Xv, B32)
+    arith = 2 * 5 * 2.0 ** -24 * R.interp_rows(np.abs(Xv), {k: (np.abs(v) if isinstance(
+        v, np.ndarray) else v) for k, v in B32.items()})
+    eps = 1.2 * math.pi * math.hypot(1 / 262143, 1 / (2 * 131071)) + 2.0 ** -22 + 2.0 ** -23
+    nrm = np.linalg.norm(ref, axis=-1, keepdims=True) + np.linalg.norm(arith, axis=-1,
+                                                                       keepdims=True)
+    assert np.all(np.abs(got - ref) <= arith + eps * nrm + 1e-30)
+    del Wx, out
+    # step 8: interface flux of the sampled elements (every flux point, both sides)
+    G = synth.device_vectors(nf * 5 * ne, 42, dev, lo=-2.0, hi=1.0).reshape(nf, 5, ne, 3)
+    Wg, _ = _fr_sample_words(fo, G, st, "step 8 gradient rows")
+    Wn = ivc.compress(fmt, c["n_f"].reshape(-1, 3)).reshape(nf, 1, ne)
+    Ws = ivc.compress(fmt, c["S_f"].reshape(-1, 3)).reshape(nf, 3, ne)
+    gas = dict(gamma=1.4, mu=1.0 / 1600.0, prandtl=0.72)
+    res = ivc.fr_common_viscous_flux(fmt, order, ivc.fr_gas(**gas), dims, Wg, Wn, Ws,
+                                     c["detJ_f"], c["q_f"], c["nFinv_f"])
+    got8 = res[:, :, st].cpu().numpy().astype(np.float64)              # (nf, 5, ns)
+    # the partners of the sampled elements' flux points, and the oracle on both sides
+    pr = R.partner(dims, order + 1)                                     # (nf, ne) flat f' ne + e'
+    pf, pe = pr[:, sel] // ne, pr[:, sel] % ne
+    fidx = np.arange(nf)[:, None].repeat(sel.size, 1)
+
+    def side(f_i, e_i):
+        ft = torch.from_numpy(np.ascontiguousarray(f_i).reshape(-1)).to(dev)
+        et = torch.from_numpy(np.ascontiguousarray(e_i).reshape(-1)).to(dev)
+        g = O.decompress(fo, Wg[ft, :, et].cpu().numpy().view(np.uint64).reshape(-1)).reshape(
+            -1, 5, 3).astype(np.float64)
+        s = O.decompress(fo, Ws[ft, :, et].cpu().numpy().view(np.uint64).reshape(-1)).reshape(
+            -1, 3, 3).astype(np.float64)
+        det = c["detJ_f"][ft, et].cpu().numpy().astype(np.float64)
+        qv = c["q_f"][ft, :, et].cpu().numpy().astype(np.float64).T      # (5, m)
+        gx = R.physical_gradient(np.moveaxis(g, 1, 0), s, det)
+        gxm = R.physical_gradient(np.moveaxis(g, 1, 0), s, det, mag=True)
+        return (R.viscous_rows(qv, gx, gas["gamma"], gas["mu"], gas["prandtl"]),
+                R.viscous_rows(qv, gxm, gas["gamma"], gas["mu"], gas["prandtl"], mag=True))
+
+    Fo, Mo = side(fidx, np.broadcast_to(sel, fidx.shape))
+    Fp, Mp = side(pf, pe)
+    ft, et = torch.from_numpy(fidx.reshape(-1)).to(dev), torch.from_numpy(
+        np.broadcast_to(sel, fidx.shape).reshape(-1).copy()).to(dev)
+    n = O.decompress(fo, Wn[ft, 0, et].cpu().numpy().view(np.uint64)).astype(np.float64)
+    nFi = c["nFinv_f"][ft, :, et].cpu().numpy().astype(np.float64).T   # (5, m)
+    ref8 = nFi - 0.5 * ((Fo + Fp) * n[None]).sum(-1)
+    mag8 = np.abs(nFi) + 0.5 * ((Mo + Mp) * np.abs(n)[None]).sum(-1)
+    ref8 = np.moveaxis(ref8.reshape(5, nf, sel.size), 0, 1)
+    mag8 = np.moveaxis(mag8.reshape(5, nf, sel.size), 0, 1)
+    assert np.all(np.abs(got8 - ref8) <= 64 * 2.0 ** -24 * mag8 + 1e-30)
