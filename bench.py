@@ -739,6 +739,12 @@ def run_fdiv(args):
                             warmup, stream)
     ms32, per32 = time_launches(lambda: ivc.f32_flux_divergence(Fc, D, out=out32, stream=s),
                                 steps, warmup, stream)
+    # the same two on the CUDA cores (FP32 FMAs)
+    out_s = torch.empty_like(out)
+    ms_s, _ = time_launches(lambda: ivc.flux_divergence(fmt, W, D, out=out_s, stream=s,
+                                                        simt=True), steps, warmup, stream)
+    ms32_s, _ = time_launches(lambda: ivc.f32_flux_divergence(Fc, D, out=out_s, stream=s,
+                                                              simt=True), steps, warmup, stream)
     ivc.flux_divergence_check()
     t, t32 = ms / steps, ms32 / steps
     flop = 2.0 * 3 * ns * ns * nv                                   # per element
@@ -760,6 +766,10 @@ def run_fdiv(args):
             "fp32_ms": round(t32, 4), "fp32_gbs_algorithmic": round(bytes_32 * ne / (t32 * 1e-3) / 1e9, 1),
             "fp32_tflops": round(flop * ne / (t32 * 1e-3) / 1e12, 2),
             "speedup_vs_fp32": round(t32 / t, 4),
+            "engine": "tensor cores (tcgen05 kind::tf32, 3 products per FP32 term)",
+            "simt_ms": round(ms_s / steps, 4), "simt_fp32_ms": round(ms32_s / steps, 4),
+            "tc_speedup_vs_simt": round(ms_s / ms, 4),
+            "tc_fp32_speedup_vs_simt": round(ms32_s / ms32, 4),
             "max_abs_diff_vs_fp32_input": float(d.max()), "max_abs_fp32_result": float(scale),
             "bytes_per_element": {"compressed": bytes_c, "fp32": bytes_32},
             "data": "synthetic TGV initial state (Sec. 4.2), Euler flux rows, degree-3 hexes"}

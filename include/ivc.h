@@ -262,10 +262,20 @@ ivc_status ivc_f32_gather(ivc_layout layout, const float *src, int64_t ld, int64
  *        ld_out >= ne; entries with e >= ne are not written.
  * Limits: 1 <= ns <= 64 (hex elements up to degree 3), 1 <= nvars <= 5.
  * Errors: IVC_ERR_ARG for sizes out of range or NULL pointers with ne > 0,
- * IVC_ERR_ALIGN for F not 8-byte or D / div not 4-byte aligned. */
+ * IVC_ERR_ALIGN for F not 8-byte or D / div not 4-byte aligned.
+ * The products run on the tensor cores (tcgen05, FP32 accumulation, each FP32
+ * operand split into a TF32 head and tail: three TF32 products per term, the
+ * result within the FP32 summation bound above). */
 ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
                                int nvars, int64_t ne, const float *D, float *div,
                                int64_t ld_out, ivc_stream_t stream);
+
+/* The same divergence with FP32 FMAs on the CUDA cores (a block of decoding
+ * warps and FMA warps handing buffers over through mbarriers), kept for
+ * comparison; same arguments, limits and errors. */
+ivc_status ivc_flux_divergence_simt(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
+                                    int nvars, int64_t ne, const float *D, float *div,
+                                    int64_t ld_out, ivc_stream_t stream);
 
 /* Reports (and clears) a failure of the flux-divergence kernels since the
  * last check: their decoding and accumulating warps hand shared-memory
@@ -280,6 +290,10 @@ ivc_status ivc_flux_divergence_check(void);
 ivc_status ivc_f32_flux_divergence(const float *F, int64_t ld, int ns, int nvars, int64_t ne,
                                    const float *D, float *div, int64_t ld_out,
                                    ivc_stream_t stream);
+/* ... and its CUDA-core counterpart. */
+ivc_status ivc_f32_flux_divergence_simt(const float *F, int64_t ld, int ns, int nvars,
+                                        int64_t ne, const float *D, float *div, int64_t ld_out,
+                                        ivc_stream_t stream);
 
 /* The compressed add c = a + b (Sec. 5) of HOST-resident words: a, b, c are
  * host pointers.  When all three are page-locked (cudaHostAlloc or

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libivc.so")
 SOURCES = ["ivc_ops.cu", "ivc_api.cu", "ivc_baseline.cu", "ivc_noalloc.cu", "ivc_fdiv.cu",
-           "ivc_host.cu", "ivc_gather.cu", "ivc_fr.cu"]
+           "ivc_host.cu", "ivc_gather.cu", "ivc_fr.cu", "ivc_fdiv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"]

@@ -509,9 +509,11 @@ ivc_status fdiv_args(const void *F, int64_t ld, int ns, int nvars, int64_t ne, c
 
 }  // namespace
 
-ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
-                               int nvars, int64_t ne, const float *D, float *div,
-                               int64_t ld_out, ivc_stream_t stream) {
+namespace {
+
+ivc_status flux_divergence(bool tc, const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
+                           int nvars, int64_t ne, const float *D, float *div, int64_t ld_out,
+                           ivc_stream_t stream) {
   DevFormat Fm;
   int map;
   ivc_status st = ivc::format_fields(fmt, &Fm, &map);  // no device work yet
@@ -521,27 +523,54 @@ ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t
   st = make_devformat(fmt, &Fm, &map);
   if (st != IVC_OK) return st;
   const bool fastp = fast::fast_geometry(map, Fm) == 1;
-  return cuda_status(launch_flux_div(map, fastp, false, Fm, F, ld, ns, nvars, ne, D, div, ld_out,
-                                     stream));
+  return cuda_status((tc ? launch_flux_div_tc : launch_flux_div)(map, fastp, false, Fm, F, ld, ns,
+                                                                 nvars, ne, D, div, ld_out,
+                                                                 stream));
+}
+
+ivc_status f32_flux_divergence(bool tc, const float *F, int64_t ld, int ns, int nvars, int64_t ne,
+                               const float *D, float *div, int64_t ld_out, ivc_stream_t stream) {
+  ivc_status st = fdiv_args(F, ld, ns, nvars, ne, D, div, ld_out, 4);
+  if (st != IVC_OK || ne == 0) return st;
+  DevFormat none{};
+  return cuda_status((tc ? launch_flux_div_tc : launch_flux_div)(IVC_MAP_UNIFORM, false, true,
+                                                                 none, F, ld, ns, nvars, ne, D,
+                                                                 div, ld_out, stream));
+}
+
+}  // namespace
+
+ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
+                               int nvars, int64_t ne, const float *D, float *div,
+                               int64_t ld_out, ivc_stream_t stream) {
+  return flux_divergence(true, fmt, F, ld, ns, nvars, ne, D, div, ld_out, stream);
+}
+
+ivc_status ivc_flux_divergence_simt(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
+                                    int nvars, int64_t ne, const float *D, float *div,
+                                    int64_t ld_out, ivc_stream_t stream) {
+  return flux_divergence(false, fmt, F, ld, ns, nvars, ne, D, div, ld_out, stream);
 }
 
 ivc_status ivc_flux_divergence_check(void) {
-  int status = 0;
-  if (flux_div_status(&status) != cudaSuccess) {
+  int status = 0, status_tc = 0;
+  if (flux_div_status(&status) != cudaSuccess || flux_div_tc_status(&status_tc) != cudaSuccess) {
     cudaGetLastError();
     return IVC_ERR_CUDA;
   }
-  return status ? IVC_ERR_TIMEOUT : IVC_OK;
+  return (status || status_tc) ? IVC_ERR_TIMEOUT : IVC_OK;
 }
 
 ivc_status ivc_f32_flux_divergence(const float *F, int64_t ld, int ns, int nvars, int64_t ne,
                                    const float *D, float *div, int64_t ld_out,
                                    ivc_stream_t stream) {
-  ivc_status st = fdiv_args(F, ld, ns, nvars, ne, D, div, ld_out, 4);
-  if (st != IVC_OK || ne == 0) return st;
-  DevFormat none{};
-  return cuda_status(launch_flux_div(IVC_MAP_UNIFORM, false, true, none, F, ld, ns, nvars, ne, D,
-                                     div, ld_out, stream));
+  return f32_flux_divergence(true, F, ld, ns, nvars, ne, D, div, ld_out, stream);
+}
+
+ivc_status ivc_f32_flux_divergence_simt(const float *F, int64_t ld, int ns, int nvars, int64_t ne,
+                                        const float *D, float *div, int64_t ld_out,
+                                        ivc_stream_t stream) {
+  return f32_flux_divergence(false, F, ld, ns, nvars, ne, D, div, ld_out, stream);
 }
 
 // ------------------------------------------------- flux reconstruction (5-11)

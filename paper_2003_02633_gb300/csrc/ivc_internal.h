@@ -122,6 +122,14 @@ struct FrCall {
 };
 cudaError_t launch_fr(const FrCall &call, cudaStream_t st);
 
+// The same divergence on the tensor cores (tcgen05, TF32 head/tail split of
+// the FP32 operands); the launcher sizes its own grid (one block per tile of
+// 128 elements).
+cudaError_t launch_flux_div_tc(int map, bool fast_path, bool f32, const DevFormat &F,
+                               const void *src, int64_t ld, int ns, int nv, int64_t ne,
+                               const float *D, float *div, int64_t ld_out, cudaStream_t st);
+cudaError_t flux_div_tc_status(int *status);
+
 // Reads and clears the flux-divergence kernels' device status word (1: a
 // bounded wait between the decoding and the accumulating warps ran out).
 cudaError_t flux_div_status(int *status);

@@ -98,7 +98,9 @@ _SIGS = {
     "ivc_tune": [_FMT, _I, _P, _P, _P, _I64, _P, ctypes.POINTER(ivc_launch_config)],
     "ivc_add_noalloc": [_FMT, _P, _P, _P, _I64, _P],
     "ivc_flux_divergence": [_FMT, _P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
+    "ivc_flux_divergence_simt": [_FMT, _P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
     "ivc_f32_flux_divergence": [_P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
+    "ivc_f32_flux_divergence_simt": [_P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
     "ivc_add_host": [_FMT, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P],
     "ivc_flux_divergence_check": [],
     "ivc_gather_decompress": [_FMT, _P, _I64, _P, _I64, _P, _P],
@@ -228,19 +230,20 @@ def add(fmt, a, b, out=None, cfg=None, stream=None):
     return out
 
 
-def flux_divergence(fmt, F, D, ne=None, out=None, stream=None):
+def flux_divergence(fmt, F, D, ne=None, out=None, stream=None, simt=False):
     """Algorithm 1: divergence of a compressed flux.  F: int64 words of shape
     (ns, nvars, ld) (element index fastest; the first ``ne`` elements are
     used, default all); D: float32 (3 ns, ns).  Returns float32
-    (ns, nvars, ld_out) with ld_out = out.shape[2] (default ld)."""
+    (ns, nvars, ld_out) with ld_out = out.shape[2] (default ld).  ``simt``
+    selects the CUDA-core kernel instead of the tensor-core one."""
     import torch
     ns, nv, ld = F.shape
     ne = ld if ne is None else int(ne)
     if out is None:
         out = torch.empty((ns, nv, ld), dtype=torch.float32, device=F.device)
-    _chk(load().ivc_flux_divergence(ctypes.byref(fmt), _ptr(F), ld, ns, nv, ne, _ptr(D),
-                                    _ptr(out), out.shape[2], _stream(stream)),
-         "ivc_flux_divergence")
+    name = "ivc_flux_divergence_simt" if simt else "ivc_flux_divergence"
+    _chk(getattr(load(), name)(ctypes.byref(fmt), _ptr(F), ld, ns, nv, ne, _ptr(D), _ptr(out),
+                               out.shape[2], _stream(stream)), name)
     return out
 
 
@@ -250,7 +253,7 @@ def flux_divergence_check():
     _chk(load().ivc_flux_divergence_check(), "ivc_flux_divergence_check")
 
 
-def f32_flux_divergence(F, D, ne=None, out=None, stream=None):
+def f32_flux_divergence(F, D, ne=None, out=None, stream=None, simt=False):
     """Algorithm 1 on an uncompressed flux: F float32 of shape (3, ns, nvars, ld)
     (component c of row (j, p) of element e at F[c, j, p, e])."""
     import torch
@@ -258,9 +261,9 @@ def f32_flux_divergence(F, D, ne=None, out=None, stream=None):
     ne = ld if ne is None else int(ne)
     if out is None:
         out = torch.empty((ns, nv, ld), dtype=torch.float32, device=F.device)
-    _chk(load().ivc_f32_flux_divergence(_ptr(F), ld, ns, nv, ne, _ptr(D), _ptr(out),
-                                        out.shape[2], _stream(stream)),
-         "ivc_f32_flux_divergence")
+    name = "ivc_f32_flux_divergence_simt" if simt else "ivc_f32_flux_divergence"
+    _chk(getattr(load(), name)(_ptr(F), ld, ns, nv, ne, _ptr(D), _ptr(out), out.shape[2],
+                               _stream(stream)), name)
     return out
 
 

@@ -1,5 +1,7 @@
 """GPU parity of the compressed flux divergence (Algorithm 1, Sec. 4; Table
-fr_nse, step 10) against the oracle, through the C ABI.
+fr_nse, step 10) against the oracle, through the C ABI: the tensor-core kernel
+(ivc_flux_divergence: three TF32 products per FP32 term, FP32 accumulation)
+and the CUDA-core one (ivc_flux_divergence_simt), both held to the bound below.
 
 The oracle compresses the FP32 flux itself and the GPU is given the oracle's
 words.  The GPU accumulates the 3 ns products of each output in FP32 (FMA,
@@ -39,7 +41,7 @@ def _bound(D, X, ns):
     return 2.0 * (3 * ns + 2) * U * t + 1e-30
 
 
-def _run(fname, order, ne, nvars=5, ld=None, h=2 * math.pi / 16):
+def _run(fname, order, ne, nvars=5, ld=None, h=2 * math.pi / 16, simt=False):
     fo, fg = formats(fname)
     F = _flux(order, ne, nvars)
     ns = F.shape[0]
@@ -51,7 +53,7 @@ def _run(fname, order, ne, nvars=5, ld=None, h=2 * math.pi / 16):
     Wd = torch.from_numpy(wpad.view(np.int64)).to(DEV)
     Dd = torch.from_numpy(D).to(DEV)
     out = torch.full((ns, nvars, ld), 7.0, dtype=torch.float32, device=DEV)
-    ivc.flux_divergence(fg, Wd, Dd, ne=ne, out=out)
+    ivc.flux_divergence(fg, Wd, Dd, ne=ne, out=out, simt=simt)
     ivc.flux_divergence_check()   # no bounded wait ran out
     got = out.cpu().numpy()
     ref = O.flux_divergence(fo, w, D, ns, nvars)
@@ -64,19 +66,23 @@ def _run(fname, order, ne, nvars=5, ld=None, h=2 * math.pi / 16):
     return err, bound
 
 
+@pytest.mark.parametrize("simt", [False, True])
 @pytest.mark.parametrize("fname", ["primary", "L1717", "tanh", "fracsplit"])
-def test_fdiv_formats_ragged(fname):
-    # 3 full tiles of 64 elements and a ragged one
-    _run(fname, 3, 3 * 64 + 37)
+def test_fdiv_formats_ragged(fname, simt):
+    # 3 full tiles of 64 elements and a ragged one (1 full tile of 128 and a
+    # ragged one on the tensor-core kernel)
+    _run(fname, 3, 3 * 64 + 37, simt=simt)
 
 
+@pytest.mark.parametrize("simt", [False, True])
 @pytest.mark.parametrize("order,nvars", [(1, 5), (2, 3), (3, 1), (3, 4)])
-def test_fdiv_orders_and_rows(order, nvars):
-    _run("primary", order, 100, nvars=nvars)
+def test_fdiv_orders_and_rows(order, nvars, simt):
+    _run("primary", order, 100, nvars=nvars, simt=simt)
 
 
-def test_fdiv_padded_leading_dimension():
-    _run("primary", 3, 77, ld=80)
+@pytest.mark.parametrize("simt", [False, True])
+def test_fdiv_padded_leading_dimension(simt):
+    _run("primary", 3, 77, ld=80, simt=simt)
 
 
 def test_fdiv_single_element_and_empty():
@@ -88,19 +94,23 @@ def test_fdiv_single_element_and_empty():
     assert out.shape == (64, 5, 0)
 
 
-def test_fdiv_many_tiles():
-    # 4096 + 37 elements: 65 tiles, more than one per block on small grids
-    err, bound = _run("primary", 3, 4096 + 37)
+@pytest.mark.parametrize("simt", [False, True])
+def test_fdiv_many_tiles(simt):
+    # 4096 + 37 elements: 65 tiles of 64 (more than one per block on small
+    # grids), 33 of 128
+    err, bound = _run("primary", 3, 4096 + 37, simt=simt)
     assert float((err / bound).max()) < 1.0
 
 
-def test_f32_flux_divergence_baseline():
+@pytest.mark.parametrize("simt", [False, True])
+def test_f32_flux_divergence_baseline(simt):
     order, ne, nvars = 3, 200, 5
     F = _flux(order, ne, nvars)
     ns = F.shape[0]
     D = synth.fr_hex_operator(order, 0.3)
     Fc = np.ascontiguousarray(np.transpose(F, (3, 0, 1, 2)))        # (3, ns, nvars, ne)
-    out = ivc.f32_flux_divergence(torch.from_numpy(Fc).to(DEV), torch.from_numpy(D).to(DEV))
+    out = ivc.f32_flux_divergence(torch.from_numpy(Fc).to(DEV), torch.from_numpy(D).to(DEV),
+                                  simt=simt)
     ivc.flux_divergence_check()
     got = out.cpu().numpy().astype(np.float64)
     Dd = D.astype(np.float64).reshape(3, ns, ns)
