@@ -151,7 +151,7 @@ __device__ __forceinline__ uint32_t kmajor_off(int row, int k, int rows) {
 
 constexpr int kProducers = 512;               // 16 decoding warps, one element pair each
 constexpr int kThreadsTC = kProducers + 32;    // + the warp that issues the products
-constexpr int kStages = 4;                     // A buffers in flight
+constexpr int kStages = 4;                     // A buffers in flight (a power of 2)
 
 // Shared memory: [B head | B tail | A stages (head, tail) | tables |
 //                 barriers full[S], empty[S], acc_full, acc_empty | TMEM address | abort]
@@ -187,20 +187,29 @@ struct Stage {
   int64_t ti;        // index of the tile among the block's tiles
   int ch, p;
   bool first, last;  // first / last stage of the tile
-};
 
-__device__ __forceinline__ Stage stage_of(int64_t g, int nq, int nv, int nchunk) {
-  Stage s;
-  s.ti = g / nq;
-  const int q = (int)(g - s.ti * nq);
-  s.tile = blockIdx.x + s.ti * (int64_t)gridDim.x;
-  s.ch = q / nv;
-  s.p = q - s.ch * nv;
-  s.first = q == 0;
-  s.last = q == nq - 1;
-  (void)nchunk;
-  return s;
-}
+  __device__ void start(int nchunk, int nv) {
+    ti = 0;
+    tile = blockIdx.x;
+    ch = 0;
+    p = 0;
+    first = true;
+    last = nchunk == 1 && nv == 1;
+  }
+  // the next stage: equation, then point chunk, then the block's next tile
+  __device__ void advance(int nchunk, int nv) {
+    if (++p == nv) {
+      p = 0;
+      if (++ch == nchunk) {
+        ch = 0;
+        ++ti;
+        tile += gridDim.x;
+      }
+    }
+    first = ch == 0 && p == 0;
+    last = ch == nchunk - 1 && p == nv - 1;
+  }
+};
 
 // A producer's pair of stage s: point jj = lane / 8 + 4 (warp / 8), elements
 // m = 8 (warp % 8) + lane % 8 and m + 64 of the tile.  Within a warp the
@@ -260,10 +269,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const bool producer = threadIdx.x < kProducers;
   const int jj = (lane >> 3) + 4 * (warp >> 3), m = 8 * (warp & 7) + (lane & 7);
 
-  // the first stage's loads go out before the set-up
-  PairIn<MODE> cur;
-  if (producer && niter > 0) load_pair<MODE>(cur, src, ld, ns, nv, ne, stage_of(0, nq, nv, nchunk),
-                                             jj, m);
+  // the first two stages' loads go out before the set-up
+  PairIn<MODE> cur, nxt;
+  Stage ls;                                     // the stage of the next loads
+  ls.start(nchunk, nv);
+  if (producer) {
+    if (niter > 0) load_pair<MODE>(cur, src, ld, ns, nv, ne, ls, jj, m);
+    ls.advance(nchunk, nv);
+    if (niter > 1) load_pair<MODE>(nxt, src, ld, ns, nv, ne, ls, jj, m);
+    ls.advance(nchunk, nv);
+  }
   if (warp == kProducers / 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
@@ -303,13 +318,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
   if (producer) {
     // ------------------------------------------------------------ producers
-    for (int64_t g = 0; g < niter; ++g) {
-      const Stage s = stage_of(g, nq, nv, nchunk);
-      const int b = (int)(g % kStages);
+    // this thread's A offsets (the same in every stage)
+    uint32_t offa[3], offb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      offa[c] = kmajor_off(m, 3 * jj + c, kTM);
+      offb[c] = kmajor_off(m + kTM / 2, 3 * jj + c, kTM);
+    }
+    Stage s;
+    s.start(nchunk, nv);
+    for (int64_t g = 0; g < niter; ++g, s.advance(nchunk, nv)) {
+      const int b = (int)(g & (kStages - 1));
       const uint32_t u = (uint32_t)(g / kStages);
-      PairIn<MODE> nxt = cur;
-      if (g + 1 < niter) load_pair<MODE>(nxt, src, ld, ns, nv, ne,
-                                         stage_of(g + 1, nq, nv, nchunk), jj, m);
+      // loads two stages ahead
+      PairIn<MODE> nxt2 = nxt;
+      if (g + 2 < niter) load_pair<MODE>(nxt2, src, ld, ns, nv, ne, ls, jj, m);
+      ls.advance(nchunk, nv);
       if (u >= 1 && !bar_wait(empty + b, (u - 1) & 1u)) *abort_flag = 1;
       if (*abort_flag) break;
       float xa[3], xb[3];
@@ -333,20 +357,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       unsigned char *Ah = Abase + b * 2 * kABuf, *Al = Ah + kABuf;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int kk = 3 * jj + c;
         float hi, lo;
         split_tf32(xa[c], hi, lo);
-        uint32_t off = kmajor_off(m, kk, kTM);
-        *reinterpret_cast<float *>(Ah + off) = hi;
-        *reinterpret_cast<float *>(Al + off) = lo;
+        *reinterpret_cast<float *>(Ah + offa[c]) = hi;
+        *reinterpret_cast<float *>(Al + offa[c]) = lo;
         split_tf32(xb[c], hi, lo);
-        off = kmajor_off(m + kTM / 2, kk, kTM);
-        *reinterpret_cast<float *>(Ah + off) = hi;
-        *reinterpret_cast<float *>(Al + off) = lo;
+        *reinterpret_cast<float *>(Ah + offb[c]) = hi;
+        *reinterpret_cast<float *>(Al + offb[c]) = lo;
       }
       fence_async_smem();
       bar_arrive(full + b);
       cur = nxt;
+      nxt = nxt2;
       if (s.last && warp < 4) {
         // epilogue of the tile: the accumulators, once its products are done
         if (!bar_wait(acc_full, (uint32_t)(s.ti & 1))) *abort_flag = 1;
@@ -374,9 +396,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // -------------------------------------------------------- the MMA issuer
     const uint32_t idesc = idesc_tf32(kTM, L.np);
     int64_t issued = -1;                       // last stage with products in flight
-    for (int64_t g = 0; g < niter; ++g) {
-      const Stage s = stage_of(g, nq, nv, nchunk);
-      const int b = (int)(g % kStages);
+    Stage s;
+    s.start(nchunk, nv);
+    for (int64_t g = 0; g < niter; ++g, s.advance(nchunk, nv)) {
+      const int b = (int)(g & (kStages - 1));
       const uint32_t u = (uint32_t)(g / kStages);
       if (!bar_wait(full + b, u & 1u)) *abort_flag = 1;
       // a new tile overwrites the accumulators: the previous tile's epilogue
@@ -405,7 +428,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     // all products done before the memory is freed (the last commit covers
     // every earlier product of this thread)
-    if (issued >= 0) bar_wait(empty + (int)(issued % kStages), (uint32_t)(issued / kStages) & 1u);
+    if (issued >= 0)
+      bar_wait(empty + (int)(issued & (kStages - 1)), (uint32_t)(issued / kStages) & 1u);
   }
   if (*abort_flag && threadIdx.x == 0) atomicExch(&g_fdiv_tc_status, 1);
   tc_fence_before();
