@@ -79,6 +79,21 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
 
 
+def tf32_roofline(issued_tflops: float) -> dict:
+    """TF32 tensor-core products issued against the dense TF32 peak, derived
+    from the measured bf16 peak and the nominal tf32 : bf16 ratio (1.1 : 2.25
+    PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        src = "MEASURED_PEAKS.json bf16_tflops (burst) x 1.1 / 2.25"
+    except Exception:
+        bf16, src = 1900.0, "fallback 1.9 PFLOP/s bf16 x 1.1 / 2.25"
+    peak = bf16 * 1.1 / 2.25
+    return {"issued_tf32_tflops": round(issued_tflops, 1), "peak_tf32_tflops": round(peak, 1),
+            "frac": round(issued_tflops / peak, 4), "peak_source": src}
+
+
 def issue_roofline(prof, gvec_s, clocks):
     """The bound the compressed add actually meets: warp instructions issued per
     second (instructions per vector from the committed ncu capture of the same
@@ -767,6 +782,7 @@ def run_fdiv(args):
             "fp32_tflops": round(flop * ne / (t32 * 1e-3) / 1e12, 2),
             "speedup_vs_fp32": round(t32 / t, 4),
             "engine": "tensor cores (tcgen05 kind::tf32, 3 products per FP32 term)",
+            "tensor": tf32_roofline(3 * flop * ne / (t * 1e-3) / 1e12),
             "simt_ms": round(ms_s / steps, 4), "simt_fp32_ms": round(ms32_s / steps, 4),
             "tc_speedup_vs_simt": round(ms_s / ms, 4),
             "tc_fp32_speedup_vs_simt": round(ms32_s / ms32, 4),
