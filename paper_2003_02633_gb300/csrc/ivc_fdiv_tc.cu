@@ -5,13 +5,16 @@
 // for one equation p and a tile of 128 elements, the product
 //     Out (128 x ns) = A (128 x 3 ns) B (3 ns x ns),
 // A[e][3 j + c] = X(j, p, e)_c (the decoded flux) and B[3 j + c][k] =
-// D[c ns + j][k].  Each block owns one tile: its 8 warps decode the words of
-// 8 solution points of one equation at a time into shared memory (A, K-major,
-// no swizzle: 8-row x 16-byte core matrices), thread 0 issues tcgen05.mma on
-// them (M = 128, N = ns padded to 16, K = 8 per instruction) into an FP32
-// accumulator in tensor memory (one column block per equation), and
-// tcgen05.commit releases the buffer through an mbarrier while the warps
-// decode the next points into the other buffer.  B is staged once per block.
+// D[c ns + j][k].  One persistent block per SM stages B once and walks its
+// tiles in stages of 8 solution points of one equation: 16 decoding warps
+// write a stage's A (K-major, no swizzle: 8-row x 16-byte core matrices) into
+// one of 4 shared-memory buffers and arrive on its "full" mbarrier; one thread
+// of a 17th warp waits for it, issues tcgen05.mma (M = 128, N = ns padded to
+// 16, K = 8 per instruction) into the equation's FP32 accumulator in tensor
+// memory, and tcgen05.commit releases the buffer through its "empty"
+// mbarrier.  After a tile's last stage, four decoding warps read the
+// accumulators (tcgen05.ld) and store the divergence, and the next tile's
+// first products wait on an mbarrier until they have.
 //
 // Precision: the operands are FP32 values with 24-bit significands, so each
 // is split into a TF32 head (rounded to nearest) and the FP32 remainder, and
