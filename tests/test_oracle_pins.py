@@ -3,7 +3,8 @@
 Every oracle function is pinned by at least one test here:
   encode (compress)      worked examples, Table 1 statistics, half-quantum
                          bounds, nearest-bin brute force, exact RN32 norm,
-                         Niven ties, edge cases, layout special cases
+                         Niven ties, edge cases, layout special cases, the
+                         single-precision bin-miss rates of Table C++_misses
   decode (decompress)    worked examples, norm and angle invariants,
                          first-order error model (Eq. v_error), mirror symmetry,
                          round-away bound, exhaustive idempotence at 16 bits
@@ -507,3 +508,39 @@ def test_fracsplit_sweep_within_figure_window(oracle_mod):
         assert 0.3e-5 <= st["sd"] <= 0.7e-5, (p1, st["sd"])
         means[p1] = st["mean"]
     assert min(means, key=means.get) == 1 << 17
+
+
+def test_single_precision_bin_misses(oracle_mod):
+    # Table C++_misses (Sec. 3): angles computed in single precision (atan2f,
+    # acosf of z / r) put about 0.2 % of the vectors in another bin than the
+    # exact ones; phi more often than theta.  The oracle's bins against such a
+    # pipeline (angles in FP32, the bin coordinate in FP64) must show the same
+    # rates within the spread of single-precision libm implementations
+    # (factor 1.6), and the same ordering.
+    O = oracle_mod
+    import os
+    gold = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "sp_bin_misses.txt")):
+        if line.strip() and not line.startswith("#"):
+            code, where, pct = line.split()
+            gold[(code, where)] = float(pct)
+    fo = O.PRIMARY
+    N, M = O.nmax(fo)
+    for where, x in (("S2", synth.unit_sphere(200000, seed=3)),
+                     ("cube", synth.unit_cube(200000, seed=4))):
+        x = np.asarray(x, np.float32)
+        f = O.fields(fo, O.compress(fo, x))                   # E, m, n_theta, n_phi
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        r = np.sqrt(X * X + Y * Y + Z * Z, dtype=np.float32)
+        th = np.arctan2(Y, X).astype(np.float32).astype(np.float64)
+        ph = np.arccos((Z / r).astype(np.float32)).astype(np.float32).astype(np.float64)
+        nt = np.floor(N * (0.5 + th / (2 * np.pi)) + 0.5).astype(np.int64)
+        nt[nt == N] = 0
+        npp = np.floor(M * ph / np.pi + 0.5).astype(np.int64)
+        nt[(npp == 0) | (npp == M)] = 0
+        mt = 100 * np.mean(nt != f[:, 2])
+        mp = 100 * np.mean(npp != f[:, 3])
+        for got, code in ((mt, "n_theta"), (mp, "n_phi")):
+            want = gold[(code, where)]
+            assert want / 1.6 <= got <= want * 1.6, (where, code, got, want)
+        assert mp > mt, (where, mt, mp)
