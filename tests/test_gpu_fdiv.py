@@ -116,3 +116,29 @@ def test_f32_flux_divergence_baseline(simt):
     Dd = D.astype(np.float64).reshape(3, ns, ns)
     ref = np.einsum("cjk,jpec->kpe", Dd, F.astype(np.float64))
     assert np.all(np.abs(got - ref) <= _bound(D, F, ns))
+
+
+_MULTI = {}
+
+
+@pytest.mark.parametrize("simt", [False, True])
+def test_fdiv_several_tiles_per_block(simt):
+    # 313 tiles of 128 elements (626 of 64): more tiles than SMs, so persistent
+    # blocks walk several tiles (tile hand-over of the accumulators and of the
+    # mbarrier phases); every output against the oracle
+    if not _MULTI:
+        ne = 313 * 128 - 91
+        F = _flux(3, ne)
+        D = synth.fr_hex_operator(3, 2 * math.pi / 16)
+        fo, _ = formats("primary")
+        w = O.compress(fo, F.reshape(-1, 3)).reshape(64, 5, ne)
+        X = O.decompress(fo, w.reshape(-1)).reshape(64, 5, ne, 3)
+        _MULTI.update(ne=ne, D=D, w=w, ref=O.flux_divergence(fo, w, D, 64, 5),
+                      bound=_bound(D, X, 64))
+    fo, fg = formats("primary")
+    ne, D, w = _MULTI["ne"], _MULTI["D"], _MULTI["w"]
+    Wd = torch.from_numpy(w.view(np.int64)).to(DEV)
+    out = ivc.flux_divergence(fg, Wd, torch.from_numpy(D).to(DEV), simt=simt)
+    ivc.flux_divergence_check()
+    err = np.abs(out.cpu().numpy().astype(np.float64) - _MULTI["ref"])
+    assert np.all(err <= _MULTI["bound"]), float((err / _MULTI["bound"]).max())
