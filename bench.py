@@ -34,6 +34,7 @@ UNIT = "Gvec/s"
 BYTES_PER_VEC = 24          # read two 8-byte words, write one
 FP32_BYTES_PER_VEC = 36     # read two 12-byte vectors, write one
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0    # GB300 HBM3e, nominal (the measured copy peak is the roofline)
 
 
 def parse_args():
@@ -345,6 +346,7 @@ def run_ivc(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                          "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                          "traffic": traffic, "peak_source": peak_src,
+                         "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                          "algorithmic_bytes_per_launch": BYTES_PER_VEC * n,
                          "kernel_ms": round(kernel_ms, 5)},
             "issue_roofline": issue_roofline(prof, value, clocks),
