@@ -154,7 +154,14 @@ __device__ __forceinline__ uint32_t kmajor_off(int row, int k, int rows) {
 
 constexpr int kProducers = 512;               // 16 decoding warps, one element pair each
 constexpr int kThreadsTC = kProducers + 32;    // + the warp that issues the products
-constexpr int kStages = 4;                     // A buffers in flight (a power of 2)
+// Stage shape per row type: compressed rows decode one equation per stage
+// into one of 4 buffers; FP32 rows, whose stages are only loads, take two
+// equations per stage (two buffers), fewer and longer stages being faster there.
+template <int MODE>
+struct TcShape {
+  static constexpr int kVPS = MODE == TC_F32 ? 2 : 1;     // equations per stage
+  static constexpr int kStages = MODE == TC_F32 ? 2 : 4;  // A buffers in flight (power of 2)
+};
 
 // Shared memory: [B head | B tail | A stages (head, tail) | tables |
 //                 barriers full[S], empty[S], acc_full, acc_empty | TMEM address | abort]
@@ -164,14 +171,16 @@ struct TcLayout {
   uint32_t off_a, off_tab, off_bar, total;
 };
 
+template <int MODE>
 __host__ __device__ inline TcLayout tc_layout(int ns, int ntab_bytes) {
+  constexpr int kVPS = TcShape<MODE>::kVPS, kStages = TcShape<MODE>::kStages;
   TcLayout L;
   L.nsp = pad_to(ns, kPC);
   L.np = pad_to(ns, 16);
   L.kt = 3 * L.nsp;
   L.b_bytes = (uint32_t)(L.kt / 8) * (L.np / 8) * 2 * kCoreBytes;
   L.off_a = 2 * L.b_bytes;
-  L.off_tab = L.off_a + kStages * 2 * kABuf;
+  L.off_tab = L.off_a + kStages * kVPS * 2 * kABuf;
   L.off_bar = L.off_tab + (uint32_t)pad_to(ntab_bytes, 16);
   L.total = L.off_bar + (2 * kStages + 2) * 8 + 16;
   return L;
@@ -184,7 +193,8 @@ __device__ __forceinline__ void bar_arrive(uint64_t *bar) {
 }
 
 // The stage of a block's global stage counter g: its tile (of this block's
-// tiles), point chunk ch and equation p.
+// tiles), point chunk ch and first equation p (VPS equations per stage).
+template <int VPS>
 struct Stage {
   int64_t tile;
   int64_t ti;        // index of the tile among the block's tiles
@@ -197,11 +207,12 @@ struct Stage {
     ch = 0;
     p = 0;
     first = true;
-    last = nchunk == 1 && nv == 1;
+    last = nchunk == 1 && VPS >= nv;
   }
   // the next stage: equation, then point chunk, then the block's next tile
   __device__ void advance(int nchunk, int nv) {
-    if (++p == nv) {
+    p += VPS;
+    if (p >= nv) {
       p = 0;
       if (++ch == nchunk) {
         ch = 0;
@@ -210,7 +221,7 @@ struct Stage {
       }
     }
     first = ch == 0 && p == 0;
-    last = ch == nchunk - 1 && p == nv - 1;
+    last = ch == nchunk - 1 && p + VPS >= nv;
   }
 };
 
@@ -220,29 +231,35 @@ struct Stage {
 // matrix) and the loads are runs of 8 consecutive elements.
 template <int MODE>
 struct PairIn {
-  float a[3], b[3];
-  uint64_t w0, w1;
+  static constexpr int V = TcShape<MODE>::kVPS;
+  float a[V][3], b[V][3];
+  uint64_t w0[V], w1[V];
 };
 
 template <int MODE>
 __device__ __forceinline__ void load_pair(PairIn<MODE> &in, const void *src, int64_t ld, int ns,
-                                          int nv, int64_t ne, const Stage &s, int jj, int m) {
+                                          int nv, int64_t ne,
+                                          const Stage<TcShape<MODE>::kVPS> &s, int jj, int m) {
   const int j = s.ch * kPC + jj;
   const int64_t ea = s.tile * kTM + m, eb = ea + kTM / 2;
-  const bool va = j < ns && ea < ne, vb = j < ns && eb < ne;
-  const int64_t row = ((int64_t)(j < ns ? j : 0) * nv + s.p) * ld;
-  if (MODE == TC_F32) {
-    const float *Fr = static_cast<const float *>(src);
-    const int64_t cs = (int64_t)ns * nv * ld;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      in.a[c] = va ? __ldg(Fr + row + c * cs + ea) : 0.0f;
-      in.b[c] = vb ? __ldg(Fr + row + c * cs + eb) : 0.0f;
+  for (int v = 0; v < PairIn<MODE>::V; ++v) {
+    const bool pv = s.p + v < nv;
+    const bool va = pv && j < ns && ea < ne, vb = pv && j < ns && eb < ne;
+    const int64_t row = ((int64_t)(j < ns ? j : 0) * nv + (pv ? s.p + v : 0)) * ld;
+    if (MODE == TC_F32) {
+      const float *Fr = static_cast<const float *>(src);
+      const int64_t cs = (int64_t)ns * nv * ld;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        in.a[v][c] = va ? __ldg(Fr + row + c * cs + ea) : 0.0f;
+        in.b[v][c] = vb ? __ldg(Fr + row + c * cs + eb) : 0.0f;
+      }
+    } else {
+      const uint64_t *W = static_cast<const uint64_t *>(src);
+      in.w0[v] = va ? __ldg(W + row + ea) : 0ull;
+      in.w1[v] = vb ? __ldg(W + row + eb) : 0ull;
     }
-  } else {
-    const uint64_t *W = static_cast<const uint64_t *>(src);
-    in.w0 = va ? __ldg(W + row + ea) : 0ull;
-    in.w1 = vb ? __ldg(W + row + eb) : 0ull;
   }
 }
 
@@ -253,7 +270,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                   float *__restrict__ div, int64_t ld_out, uint32_t tmem_cols) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ntab = (MODE == TC_F32 || MAP == MAP_TANH) ? 0 : F.nent_t + F.nent_p;
-  const TcLayout L = tc_layout(ns, ntab * (int)sizeof(TabEntry));
+  constexpr int kVPS = TcShape<MODE>::kVPS, kStages = TcShape<MODE>::kStages;
+  using StageT = Stage<kVPS>;
+  const TcLayout L = tc_layout<MODE>(ns, ntab * (int)sizeof(TabEntry));
   unsigned char *Bh = smem, *Bl = smem + L.b_bytes;
   unsigned char *Abase = smem + L.off_a;
   TabEntry *tabs = reinterpret_cast<TabEntry *>(smem + L.off_tab);
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (ne + kTM - 1) / kTM;
   const int nchunk = pad_to(ns, kPC) / kPC;
-  const int nq = nchunk * nv;
+  const int nq = nchunk * ((nv + kVPS - 1) / kVPS);
   const int64_t my_tiles = (int64_t)blockIdx.x < ntiles
                                ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t niter = my_tiles * nq;
@@ -274,7 +293,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
   // the first two stages' loads go out before the set-up
   PairIn<MODE> cur, nxt;
-  Stage ls;                                     // the stage of the next loads
+  StageT ls;                                    // the stage of the next loads
   ls.start(nchunk, nv);
   if (producer) {
     if (niter > 0) load_pair<MODE>(cur, src, ld, ns, nv, ne, ls, jj, m);
@@ -328,7 +347,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       offa[c] = kmajor_off(m, 3 * jj + c, kTM);
       offb[c] = kmajor_off(m + kTM / 2, 3 * jj + c, kTM);
     }
-    Stage s;
+    StageT s;
     s.start(nchunk, nv);
     for (int64_t g = 0; g < niter; ++g, s.advance(nchunk, nv)) {
       const int b = (int)(g & (kStages - 1));
@@ -339,34 +358,38 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       ls.advance(nchunk, nv);
       if (u >= 1 && !bar_wait(empty + b, (u - 1) & 1u)) *abort_flag = 1;
       if (*abort_flag) break;
-      float xa[3], xb[3];
-      if (MODE == TC_F32) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xa[c] = cur.a[c], xb[c] = cur.b[c];
-      } else {
-        float2 X, Y, Z;
-        if (MODE == TC_FAST) {
-          fast::decode2_poles<fast::GeoPrimary>(cur.w0, cur.w1, F, tab_t, tab_p, X, Y, Z);
+      for (int v = 0; v < kVPS; ++v) {
+        float xa[3], xb[3];
+        if (MODE == TC_F32) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) xa[c] = cur.a[v][c], xb[c] = cur.b[v][c];
         } else {
-          const float3 a0 = decode_word<MAP>(cur.w0, F, tab_t, tab_p);
-          const float3 a1 = decode_word<MAP>(cur.w1, F, tab_t, tab_p);
-          X = make_float2(a0.x, a1.x);
-          Y = make_float2(a0.y, a1.y);
-          Z = make_float2(a0.z, a1.z);
+          float2 X, Y, Z;
+          if (MODE == TC_FAST) {
+            fast::decode2_poles<fast::GeoPrimary>(cur.w0[v], cur.w1[v], F, tab_t, tab_p, X, Y,
+                                                  Z);
+          } else {
+            const float3 a0 = decode_word<MAP>(cur.w0[v], F, tab_t, tab_p);
+            const float3 a1 = decode_word<MAP>(cur.w1[v], F, tab_t, tab_p);
+            X = make_float2(a0.x, a1.x);
+            Y = make_float2(a0.y, a1.y);
+            Z = make_float2(a0.z, a1.z);
+          }
+          xa[0] = X.x, xa[1] = Y.x, xa[2] = Z.x;
+          xb[0] = X.y, xb[1] = Y.y, xb[2] = Z.y;
         }
-        xa[0] = X.x, xa[1] = Y.x, xa[2] = Z.x;
-        xb[0] = X.y, xb[1] = Y.y, xb[2] = Z.y;
-      }
-      unsigned char *Ah = Abase + b * 2 * kABuf, *Al = Ah + kABuf;
+        unsigned char *Ah = Abase + (b * kVPS + v) * 2 * kABuf, *Al = Ah + kABuf;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float hi, lo;
-        split_tf32(xa[c], hi, lo);
-        *reinterpret_cast<float *>(Ah + offa[c]) = hi;
-        *reinterpret_cast<float *>(Al + offa[c]) = lo;
-        split_tf32(xb[c], hi, lo);
-        *reinterpret_cast<float *>(Ah + offb[c]) = hi;
-        *reinterpret_cast<float *>(Al + offb[c]) = lo;
+        for (int c = 0; c < 3; ++c) {
+          float hi, lo;
+          split_tf32(xa[c], hi, lo);
+          *reinterpret_cast<float *>(Ah + offa[c]) = hi;
+          *reinterpret_cast<float *>(Al + offa[c]) = lo;
+          split_tf32(xb[c], hi, lo);
+          *reinterpret_cast<float *>(Ah + offb[c]) = hi;
+          *reinterpret_cast<float *>(Al + offb[c]) = lo;
+        }
       }
       fence_async_smem();
       bar_arrive(full + b);
@@ -399,7 +422,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // -------------------------------------------------------- the MMA issuer
     const uint32_t idesc = idesc_tf32(kTM, L.np);
     int64_t issued = -1;                       // last stage with products in flight
-    Stage s;
+    StageT s;
     s.start(nchunk, nv);
     for (int64_t g = 0; g < niter; ++g, s.advance(nchunk, nv)) {
       const int b = (int)(g & (kStages - 1));
@@ -411,19 +434,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         *abort_flag = 1;
       if (*abort_flag) break;
       tc_fence_after();
-      unsigned char *Ah = Abase + b * 2 * kABuf, *Al = Ah + kABuf;
-      const uint32_t d = tmem + (uint32_t)(s.p * L.np);
+      for (int v = 0; v < kVPS && s.p + v < nv; ++v) {
+        unsigned char *Ah = Abase + (b * kVPS + v) * 2 * kABuf, *Al = Ah + kABuf;
+        const uint32_t d = tmem + (uint32_t)((s.p + v) * L.np);
 #pragma unroll
-      for (int t = 0; t < kKStepsC; ++t) {
-        const int st = s.ch * kKStepsC + t;
-        const uint64_t ah = smem_desc(smem_u32(Ah + t * kAStep), kCoreBytes, 2 * kCoreBytes);
-        const uint64_t al = smem_desc(smem_u32(Al + t * kAStep), kCoreBytes, 2 * kCoreBytes);
-        const uint32_t boff = (uint32_t)st * (L.np / 8) * 2 * kCoreBytes;
-        const uint64_t bh = smem_desc(smem_u32(Bh + boff), kCoreBytes, 2 * kCoreBytes);
-        const uint64_t bl = smem_desc(smem_u32(Bl + boff), kCoreBytes, 2 * kCoreBytes);
-        mma_tf32(d, ah, bh, idesc, (s.ch > 0 || t > 0) ? 1u : 0u);
-        mma_tf32(d, ah, bl, idesc, 1u);
-        mma_tf32(d, al, bh, idesc, 1u);
+        for (int t = 0; t < kKStepsC; ++t) {
+          const int st = s.ch * kKStepsC + t;
+          const uint64_t ah = smem_desc(smem_u32(Ah + t * kAStep), kCoreBytes, 2 * kCoreBytes);
+          const uint64_t al = smem_desc(smem_u32(Al + t * kAStep), kCoreBytes, 2 * kCoreBytes);
+          const uint32_t boff = (uint32_t)st * (L.np / 8) * 2 * kCoreBytes;
+          const uint64_t bh = smem_desc(smem_u32(Bh + boff), kCoreBytes, 2 * kCoreBytes);
+          const uint64_t bl = smem_desc(smem_u32(Bl + boff), kCoreBytes, 2 * kCoreBytes);
+          mma_tf32(d, ah, bh, idesc, (s.ch > 0 || t > 0) ? 1u : 0u);
+          mma_tf32(d, ah, bl, idesc, 1u);
+          mma_tf32(d, al, bh, idesc, 1u);
+        }
       }
       mma_commit(empty + b);
       if (s.last) mma_commit(acc_full);
@@ -449,7 +474,7 @@ template <int MODE, int MAP>
 cudaError_t launch_tc(const DevFormat &F, const void *src, int64_t ld, int ns, int nv, int64_t ne,
                       const float *D, float *div, int64_t ld_out, cudaStream_t st) {
   const int ntab = (MODE == TC_F32 || MAP == MAP_TANH) ? 0 : F.nent_t + F.nent_p;
-  const TcLayout L = tc_layout(ns, ntab * (int)sizeof(TabEntry));
+  const TcLayout L = tc_layout<MODE>(ns, ntab * (int)sizeof(TabEntry));
   // one block per SM (the tensor-memory allocation assumes it): at least
   // 120 KB of shared memory
   const size_t smem = L.total < 120u * 1024u ? 120u * 1024u : L.total;
