@@ -367,8 +367,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         } else {
           float2 X, Y, Z;
           if (MODE == TC_FAST) {
-            fast::decode2_poles<fast::GeoPrimary>(cur.w0[v], cur.w1[v], F, tab_t, tab_p, X, Y,
-                                                  Z);
+            fast::decode2_near<fast::GeoPrimary>(cur.w0[v], cur.w1[v], F, tab_t, tab_p, X, Y,
+                                                 Z);
           } else {
             const float3 a0 = decode_word<MAP>(cur.w0[v], F, tab_t, tab_p);
             const float3 a1 = decode_word<MAP>(cur.w1[v], F, tab_t, tab_p);
