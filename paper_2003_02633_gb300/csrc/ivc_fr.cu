@@ -100,7 +100,7 @@ struct FastRows {
     return Raw{v0 ? __ldg(src + i0) : 0ull, v1 ? __ldg(src + i1) : 0ull};
   }
   __device__ void decode_raw(const Raw &r, float2 &X, float2 &Y, float2 &Z) const {
-    fast::decode2_poles<G>(r.w0, r.w1, F, tab_t, tab_p, X, Y, Z);
+    fast::decode2_near<G>(r.w0, r.w1, F, tab_t, tab_p, X, Y, Z);
   }
   __device__ void load2(const T *src, int64_t i0, int64_t i1, bool v0, bool v1, int64_t cs,
                         float2 &X, float2 &Y, float2 &Z) const {
