@@ -81,7 +81,9 @@ __device__ __forceinline__ void push_pair(fast::WarpQueue &wq, bool v0, bool v1,
   }
 }
 
-// Compressed rows, fast path of layout G (packed decode and encode).
+// Compressed rows, fast path of layout G: packed decode and encode; the rows
+// are decoded rounded to nearest (within 1.5 ulp of the canonical decoded
+// values, which these FP32 steps need only to within their own rounding).
 template <class G>
 struct FastRows {
   using T = uint64_t;
