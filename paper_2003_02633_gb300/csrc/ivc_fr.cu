@@ -501,15 +501,29 @@ __global__ void __launch_bounds__(kThreads) k_fr_fcorr(const __grid_constant__ D
     const int v = (int)(it % nv);
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
+    // the interface fluxes are loaded one point ahead, the first before the
+    // staging, so that their latency overlaps the work
+    auto nf_at = [&](int f) {
+      float2 r = make_float2(0.0f, 0.0f);
+      if (f < nf) {
+        const int64_t idx = ((int64_t)f * nv + v) * ld;
+        if (va) r.x = __ldg(nF + idx + ea);
+        if (vb) r.y = __ldg(nF + idx + eb);
+      }
+      return r;
+    };
+    float2 nfc = nf_at(warp);
     stage_rows<false>(codec, Fs, sx, ns, nv, v, ld, e0, ne, cs_in);
     __syncthreads();
     for (int f = warp; f < nf; f += kWarps) {
+      const float2 nfn = nf_at(f + kWarps);
       const int face = f / (q * q);
       const float2 t = line_value(sx, B, f, face >> 1, lane);
       const float sg = (face & 1) ? 1.0f : -1.0f;
       const int64_t idx = ((int64_t)f * nv + v) * ld;
-      if (va) Fc[idx + ea] = fmaf(-sg, t.x, __ldg(nF + idx + ea));
-      if (vb) Fc[idx + eb] = fmaf(-sg, t.y, __ldg(nF + idx + eb));
+      if (va) Fc[idx + ea] = fmaf(-sg, t.x, nfc.x);
+      if (vb) Fc[idx + eb] = fmaf(-sg, t.y, nfc.y);
+      nfc = nfn;
     }
     __syncthreads();
   }
