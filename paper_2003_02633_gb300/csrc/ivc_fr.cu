@@ -772,6 +772,277 @@ __global__ void __launch_bounds__(kThreads, C::kInterfaceBlocks) k_fr_commonvis(
   codec.finish();
 }
 
+// ------------------------------------------------------------ word rows of steps 8, 9
+//
+// The pointwise steps read eight compressed rows per point and side (gradient
+// rows 0-4, metric rows 5-7).  Their decode loop stays rolled (an inlined
+// decoder per row made these kernels 2-3x slower), so the rows it reads and
+// writes live in per-thread shared-memory slots instead of local memory:
+// slot s of a thread is one pair of FP32 values (elements lane and lane + 32)
+// at float2 index s * kThreads + threadIdx.x, conflict-free.  The raw words
+// arrive by cp.async, holding no registers while in flight, in slots that no
+// decode overwrites before reading them: raw row j at R + 2j, R + 2j + 1, its
+// decoded row at D + 3j .. D + 3j + 2, with R - D >= 8 (then D + 3j + 2 <
+// R + 2(j + 1) for every j < 8).  The FP32-row twins have no decode and keep
+// their rows in registers (k_fr_flux, k_fr_commonvis).
+
+constexpr int kRows = 8;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 8-byte asynchronous global-to-shared copy; bytes = 0 fills zeros without
+// reading the source.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)),
+               "l"(__cvta_generic_to_global(src)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Starts the copies of point k's raw rows (elements ea, eb; an absent element
+// reads as the zero word) into this thread's slots R + 2j, R + 2j + 1.
+__device__ __forceinline__ void fetch_rows_async(float2 *sc, int R, const uint64_t *G,
+                                                 const uint64_t *S, int k, int64_t ea,
+                                                 int64_t eb, bool va, bool vb, int64_t ld) {
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+    const uint64_t *row = j < 5 ? G + ((int64_t)k * 5 + j) * ld : S + ((int64_t)k * 3 + j - 5) * ld;
+    cp_async8(sc + (R + 2 * j) * kThreads, va ? row + ea : row, va ? 8u : 0u);
+    cp_async8(sc + (R + 2 * j + 1) * kThreads, vb ? row + eb : row, vb ? 8u : 0u);
+  }
+}
+
+// The word held in a slot (read as the slot's own type).
+__device__ __forceinline__ uint64_t slot_word(const float2 *p) {
+  const float2 t = *p;
+  return ((uint64_t)__float_as_uint(t.y) << 32) | __float_as_uint(t.x);
+}
+
+// Decodes the eight raw rows at R into pairs at D (one decoder in the code).
+template <class C>
+__device__ __forceinline__ void decode_rows(const C &codec, float2 *sc, int R, int D) {
+#pragma unroll 1
+  for (int j = 0; j < kRows; ++j) {
+    typename C::Raw r;
+    r.w0 = slot_word(sc + (R + 2 * j) * kThreads);
+    r.w1 = slot_word(sc + (R + 2 * j + 1) * kThreads);
+    float2 X, Y, Z;
+    codec.decode_raw(r, X, Y, Z);
+    sc[(D + 3 * j) * kThreads] = X;
+    sc[(D + 3 * j + 1) * kThreads] = Y;
+    sc[(D + 3 * j + 2) * kThreads] = Z;
+  }
+}
+
+template <int H>
+__device__ __forceinline__ float half_of(const float2 *p) {
+  return H ? p->y : p->x;
+}
+
+template <int H>
+__device__ __forceinline__ void set_half(float2 *p, float v) {
+  if (H) p->y = v;
+  else p->x = v;
+}
+
+// Gradient and metric rows of element half H from the decoded rows at D.
+template <int H>
+__device__ __forceinline__ void side_rows(const float2 *sc, int D, float G[5][3], float S[3][3]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G[v][i] = half_of<H>(sc + (D + 3 * v + i) * kThreads);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S[r][i] = half_of<H>(sc + (D + 15 + 3 * r + i) * kThreads);
+}
+
+// Step 9 for element half H: its flux rows replace the decoded rows 0-4 at D
+// (read in full before the first write).
+template <int H>
+__device__ __forceinline__ void half_flux(float2 *sc, int D, const float qv[5], float detJ,
+                                          const FrGasDev &gas) {
+  float G[5][3], S[3][3], Fo[5][3];
+  side_rows<H>(sc, D, G, S);
+  point_flux(qv, G, S, detJ, gas, Fo);
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) set_half<H>(sc + (D + 3 * v + i) * kThreads, Fo[v][i]);
+}
+
+// Step 8 for element half H of one side: its viscous rows 1-4 replace the
+// decoded slots D .. D + 11.
+template <int H>
+__device__ __forceinline__ void half_viscous(float2 *sc, int D, const float qv[5], float detJ,
+                                             const FrGasDev &gas) {
+  float G[5][3], S[3][3], gx[5][3], Fv[4][3];
+  side_rows<H>(sc, D, G, S);
+  physical_gradient(G, S, detJ, gx);
+  viscous_rows(qv, gx, gas, Fv);
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) set_half<H>(sc + (D + 3 * b + a) * kThreads, Fv[b][a]);
+}
+
+// Conserved variables and |J| of point k for both elements (1 when absent).
+__device__ __forceinline__ void point_scalars(const float *qsrc, const float *detJ, int k,
+                                              int64_t ea, int64_t eb, bool va, bool vb,
+                                              int64_t ld, float qa[5], float qb[5], float &ja,
+                                              float &jb) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const int64_t idx = ((int64_t)k * 5 + v) * ld;
+    qa[v] = va ? __ldg(qsrc + idx + ea) : 1.0f;
+    qb[v] = vb ? __ldg(qsrc + idx + eb) : 1.0f;
+  }
+  ja = va ? __ldg(detJ + (int64_t)k * ld + ea) : 1.0f;
+  jb = vb ? __ldg(detJ + (int64_t)k * ld + eb) : 1.0f;
+}
+
+constexpr int kFluxSlots = 24;       // step 9: decoded rows 0-23, raw rows 8-23
+constexpr int kInterfaceSlots = 44;  // step 8: see k_fr_commonvis_w
+
+// Step 9 on compressed rows (same results as k_fr_flux).
+template <class C>
+__global__ void __launch_bounds__(kThreads) k_fr_flux_w(const __grid_constant__ DevFormat F,
+                                                        FrGasDev gas, FrSmem L, int ns,
+                                                        const float *__restrict__ qs,
+                                                        const uint64_t *G, const uint64_t *S,
+                                                        const float *__restrict__ detJ,
+                                                        int64_t ne, int64_t ld, uint64_t *Fs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  C codec = CodecOf<C>::make(F, smem, L);
+  float2 *sc = reinterpret_cast<float2 *>(smem + L.off_stage) + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ntiles = (ne + kTile - 1) / kTile;
+  const int64_t items = ntiles * ns;                        // (tile, point) per warp
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
+  for (int64_t it = gw; it < items; it += nw) {
+    const int64_t e0 = (it / ns) * kTile;
+    const int k = (int)(it % ns);
+    const int64_t ea = e0 + lane, eb = e0 + lane + 32;
+    const bool va = ea < ne, vb = eb < ne;
+    fetch_rows_async(sc, 8, G, S, k, ea, eb, va, vb, ld);
+    cp_async_commit();
+    float qa[5], qb[5], ja, jb;
+    point_scalars(qs, detJ, k, ea, eb, va, vb, ld, qa, qb, ja, jb);
+    cp_async_wait<0>();
+    decode_rows(codec, sc, 8, 0);
+    half_flux<0>(sc, 0, qa, ja, gas);
+    half_flux<1>(sc, 0, qb, jb, gas);
+#pragma unroll 1
+    for (int v = 0; v < 5; ++v) {
+      const int64_t idx = ((int64_t)k * 5 + v) * ld;
+      codec.store2(Fs, idx + ea, idx + eb, va, vb, 0, sc[(3 * v) * kThreads],
+                   sc[(3 * v + 1) * kThreads], sc[(3 * v + 2) * kThreads]);
+    }
+  }
+  codec.finish();
+}
+
+// Step 8 on compressed rows (same results and pairing of the sides as
+// k_fr_commonvis).  Slots: this side's rows decoded at 0-23 from raw 8-23, its
+// viscous rows then at 0-11; the other side's raw rows at 24-39, copied while
+// this side is decoded, decoded at 12-35, viscous rows at 12-23; the two
+// normal rows raw at 40-43.
+template <class C>
+__global__ void __launch_bounds__(kThreads, 2) k_fr_commonvis_w(
+    const __grid_constant__ DevFormat F, FrGasDev gas, FrSmem L, int q, int Ex, int Ey, int Ez,
+    const uint64_t *G, const uint64_t *nrm, const uint64_t *S, const float *__restrict__ detJ,
+    const float *__restrict__ qf, const float *__restrict__ nFinv, int64_t ne, int64_t ld,
+    float *out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  C codec = CodecOf<C>::make(F, smem, L);
+  float2 *sc = reinterpret_cast<float2 *>(smem + L.off_stage) + threadIdx.x;
+  const int nplus = 3 * q * q;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ntiles = (ne + kTile - 1) / kTile;
+  const int64_t items = ntiles * nplus;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
+  for (int64_t it = gw; it < items; it += nw) {
+    const int64_t e0 = (it / nplus) * kTile;
+    const int j = (int)(it % nplus);                // + face point: axis c, in-face index
+    const int c = j / (q * q);
+    const int f = (2 * c + 1) * q * q + j % (q * q), fo = f - q * q;
+    const int64_t ea = e0 + lane, eb = e0 + lane + 32;
+    const bool va = ea < ne, vb = eb < ne;
+    const int64_t pa = va ? neighbour(ea, c, 1, Ex, Ey, Ez) : 0;
+    const int64_t pb = vb ? neighbour(eb, c, 1, Ex, Ey, Ez) : 0;
+    const uint64_t *nf = nrm + (int64_t)f * ld, *no = nrm + (int64_t)fo * ld;
+    fetch_rows_async(sc, 8, G, S, f, ea, eb, va, vb, ld);
+    cp_async8(sc + 40 * kThreads, va ? nf + ea : nf, va ? 8u : 0u);
+    cp_async8(sc + 41 * kThreads, vb ? nf + eb : nf, vb ? 8u : 0u);
+    cp_async8(sc + 42 * kThreads, va ? no + pa : no, va ? 8u : 0u);
+    cp_async8(sc + 43 * kThreads, vb ? no + pb : no, vb ? 8u : 0u);
+    cp_async_commit();
+    fetch_rows_async(sc, 24, G, S, fo, pa, pb, va, vb, ld);
+    cp_async_commit();
+    float qa[5], qb[5], ja, jb, pqa[5], pqb[5], pja, pjb;
+    point_scalars(qf, detJ, f, ea, eb, va, vb, ld, qa, qb, ja, jb);
+    point_scalars(qf, detJ, fo, pa, pb, va, vb, ld, pqa, pqb, pja, pjb);
+    cp_async_wait<1>();
+    decode_rows(codec, sc, 8, 0);
+    half_viscous<0>(sc, 0, qa, ja, gas);
+    half_viscous<1>(sc, 0, qb, jb, gas);
+    cp_async_wait<0>();
+    decode_rows(codec, sc, 24, 12);
+    half_viscous<0>(sc, 12, pqa, pja, gas);
+    half_viscous<1>(sc, 12, pqb, pjb, gas);
+    float2 nx, ny, nz, mx, my, mz;
+    codec.decode_raw(typename C::Raw{slot_word(sc + 40 * kThreads), slot_word(sc + 41 * kThreads)},
+                     nx, ny, nz);
+    codec.decode_raw(typename C::Raw{slot_word(sc + 42 * kThreads), slot_word(sc + 43 * kThreads)},
+                     mx, my, mz);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int64_t idx = ((int64_t)f * 5 + v) * ld, ido = ((int64_t)fo * 5 + v) * ld;
+      if (v == 0) {
+        if (va) {
+          out[idx + ea] = __ldg(nFinv + idx + ea);
+          out[ido + pa] = __ldg(nFinv + ido + pa);
+        }
+        if (vb) {
+          out[idx + eb] = __ldg(nFinv + idx + eb);
+          out[ido + pb] = __ldg(nFinv + ido + pb);
+        }
+        continue;
+      }
+      float2 s[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float2 u = sc[(3 * (v - 1) + a) * kThreads], w = sc[(12 + 3 * (v - 1) + a) * kThreads];
+        s[a] = make_float2(u.x + w.x, u.y + w.y);
+      }
+      if (va) {
+        out[idx + ea] = fmaf(-0.5f, fmaf(nz.x, s[2].x, fmaf(ny.x, s[1].x, nx.x * s[0].x)),
+                             __ldg(nFinv + idx + ea));
+        out[ido + pa] = fmaf(-0.5f, fmaf(mz.x, s[2].x, fmaf(my.x, s[1].x, mx.x * s[0].x)),
+                             __ldg(nFinv + ido + pa));
+      }
+      if (vb) {
+        out[idx + eb] = fmaf(-0.5f, fmaf(nz.y, s[2].y, fmaf(ny.y, s[1].y, nx.y * s[0].y)),
+                             __ldg(nFinv + idx + eb));
+        out[ido + pb] = fmaf(-0.5f, fmaf(mz.y, s[2].y, fmaf(my.y, s[1].y, mx.y * s[0].y)),
+                             __ldg(nFinv + ido + pb));
+      }
+    }
+  }
+  codec.finish();
+}
+
 // ------------------------------------------------------------ launchers
 
 int sm_count() {
@@ -895,26 +1166,49 @@ cudaError_t launch_fr(const FrCall &a, cudaStream_t st) {
         break;
       }
       case 9: {
-        const FrSmem L = smem_plan<C>(a.F, a.map, 0, &smem);
         const int64_t warps = ntiles * ns;
-        if ((e = launch_shape(k_fr_flux<C>, smem, (warps + kWarps - 1) / kWarps, &grid)) !=
-            cudaSuccess)
-          return e;
-        k_fr_flux<C><<<grid, kThreads, smem, st>>>(a.F, gas, L, ns, (const float *)a.in0,
-                                                   (const T *)a.in1, (const T *)a.in2,
-                                                   (const float *)a.in3, a.ne, a.ld, (T *)a.out);
+        if constexpr (C::kWords) {
+          const FrSmem L = smem_plan<C>(a.F, a.map, (size_t)kFluxSlots * kThreads * 8, &smem);
+          if ((e = launch_shape(k_fr_flux_w<C>, smem, (warps + kWarps - 1) / kWarps, &grid)) !=
+              cudaSuccess)
+            return e;
+          k_fr_flux_w<C><<<grid, kThreads, smem, st>>>(
+              a.F, gas, L, ns, (const float *)a.in0, (const uint64_t *)a.in1,
+              (const uint64_t *)a.in2, (const float *)a.in3, a.ne, a.ld, (uint64_t *)a.out);
+        } else {
+          const FrSmem L = smem_plan<C>(a.F, a.map, 0, &smem);
+          if ((e = launch_shape(k_fr_flux<C>, smem, (warps + kWarps - 1) / kWarps, &grid)) !=
+              cudaSuccess)
+            return e;
+          k_fr_flux<C><<<grid, kThreads, smem, st>>>(a.F, gas, L, ns, (const float *)a.in0,
+                                                     (const T *)a.in1, (const T *)a.in2,
+                                                     (const float *)a.in3, a.ne, a.ld,
+                                                     (T *)a.out);
+        }
         break;
       }
       case 8: {
-        const FrSmem L = smem_plan<C>(a.F, a.map, 0, &smem, false);
         const int64_t warps = ntiles * (nf / 2);
-        if ((e = launch_shape(k_fr_commonvis<C>, smem, (warps + kWarps - 1) / kWarps, &grid)) !=
-            cudaSuccess)
-          return e;
-        k_fr_commonvis<C><<<grid, kThreads, smem, st>>>(
-            a.F, gas, L, q, a.dims[0], a.dims[1], a.dims[2], (const T *)a.in0, (const T *)a.in1,
-            (const T *)a.in2, (const float *)a.in3, (const float *)a.in4, (const float *)a.in5,
-            a.ne, a.ld, (float *)a.out);
+        if constexpr (C::kWords) {
+          const FrSmem L =
+              smem_plan<C>(a.F, a.map, (size_t)kInterfaceSlots * kThreads * 8, &smem, false);
+          if ((e = launch_shape(k_fr_commonvis_w<C>, smem, (warps + kWarps - 1) / kWarps,
+                                &grid)) != cudaSuccess)
+            return e;
+          k_fr_commonvis_w<C><<<grid, kThreads, smem, st>>>(
+              a.F, gas, L, q, a.dims[0], a.dims[1], a.dims[2], (const uint64_t *)a.in0,
+              (const uint64_t *)a.in1, (const uint64_t *)a.in2, (const float *)a.in3,
+              (const float *)a.in4, (const float *)a.in5, a.ne, a.ld, (float *)a.out);
+        } else {
+          const FrSmem L = smem_plan<C>(a.F, a.map, 0, &smem, false);
+          if ((e = launch_shape(k_fr_commonvis<C>, smem, (warps + kWarps - 1) / kWarps,
+                                &grid)) != cudaSuccess)
+            return e;
+          k_fr_commonvis<C><<<grid, kThreads, smem, st>>>(
+              a.F, gas, L, q, a.dims[0], a.dims[1], a.dims[2], (const T *)a.in0,
+              (const T *)a.in1, (const T *)a.in2, (const float *)a.in3, (const float *)a.in4,
+              (const float *)a.in5, a.ne, a.ld, (float *)a.out);
+        }
         break;
       }
       default:

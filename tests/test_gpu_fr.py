@@ -203,9 +203,15 @@ def test_interp_rows(name, dims, order):
 
 # ------------------------------------------------------------------ step 9
 
-@pytest.mark.parametrize("name", FMTS)
-def test_solution_flux(name):
-    C = case()
+# 20^3 elements: several (tile, point) items per warp at the full launch, so
+# that each warp reuses its staging slots from one item to the next
+MANY = (20, 20, 20)
+
+
+@pytest.mark.parametrize("name,dims", [(n, (6, 5, 4)) for n in FMTS] +
+                         [("primary", MANY), ("fracsplit", MANY)])
+def test_solution_flux(name, dims):
+    C = case(dims, 3)
     fo, fg = _fmt(name)
     Gc = R.correct_gradient(R.gradient(C.c["w_s"], C.B), C.c["dw_f"], C.B)
     Gd, Gv = C.rows_in(fo, Gc)
@@ -221,8 +227,8 @@ def test_solution_flux(name):
 
 # ------------------------------------------------------------------ step 8
 
-@pytest.mark.parametrize("name", FMTS)
-@pytest.mark.parametrize("dims", [(6, 5, 4), (1, 3, 2)])
+@pytest.mark.parametrize("name,dims", [(n, d) for n in FMTS for d in [(6, 5, 4), (1, 3, 2)]] +
+                         [("primary", MANY), ("fracsplit", MANY)])
 def test_common_viscous_flux(name, dims):
     C = case(dims, 3)
     fo, fg = _fmt(name)
