@@ -23,7 +23,9 @@
 // the tensor-product operators in sum-factorised form (q terms per output, the
 // 1-D basis in the kernel's parameter space) and encode two outputs per
 // thread (packed fast path, exact tests deferred to the per-warp queue).  The
-// pointwise steps (6, 8, 9) decode, compute in FP32 and encode in registers.
+// pointwise step 6 decodes, computes in FP32 and encodes in registers; the
+// pointwise steps 8 and 9 stage compressed rows in per-thread shared-memory
+// slots (k_fr_commonvis_w, k_fr_flux_w) and FP32 rows in registers.
 #include "ivc_decode_poles.cuh"
 #include "ivc_internal.h"
 
@@ -89,8 +91,6 @@ struct FastRows {
   using T = uint64_t;
   static constexpr bool kWords = true;
   static constexpr bool kQueue = true;
-  static constexpr int kInterfaceBlocks = 2;  // resident blocks asked of step 8 (registers)
-  static constexpr int MAP = G::MAP;
   const DevFormat &F;
   const TabEntry *tab_t, *tab_p;
   fast::WarpQueue wq;
@@ -125,7 +125,6 @@ struct GenericRows {
   using T = uint64_t;
   static constexpr bool kWords = true;
   static constexpr bool kQueue = false;
-  static constexpr int kInterfaceBlocks = 1;
   static constexpr int MAP = MAP_;
   const DevFormat &F;
   const TabEntry *tab_t, *tab_p;
@@ -161,8 +160,6 @@ struct F32Rows {
   using T = float;
   static constexpr bool kWords = false;
   static constexpr bool kQueue = false;
-  static constexpr int kInterfaceBlocks = 1;
-  static constexpr int MAP = MAP_UNIFORM;
 
   struct Raw {
     float2 x, y, z;
@@ -385,7 +382,7 @@ __device__ __forceinline__ void stage_rows(const C &codec, const typename C::T *
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ea = e0 + lane, eb = e0 + lane + 32;
   const bool va = ea < ne, vb = eb < ne;
-  if (!AHEAD) {
+  if constexpr (!AHEAD) {
     for (int k = warp; k < ns; k += kWarps) {
       const int64_t idx = ((int64_t)k * nv + v) * ld;
       float2 X0, Y0, Z0;
@@ -398,31 +395,31 @@ __device__ __forceinline__ void stage_rows(const C &codec, const typename C::T *
       s[2 * kTile + lane] = Z0.x;
       s[2 * kTile + lane + 32] = Z0.y;
     }
-    return;
-  }
-  // all of this warp's loads first, then the decodes
-  typename C::Raw raw[kPer];
+  } else {
+    // all of this warp's loads first, then the decodes
+    typename C::Raw raw[kPer];
 #pragma unroll
-  for (int i = 0; i < kPer; ++i) {
-    const int k = warp + i * kWarps;
-    if (k < ns) {
-      const int64_t idx = ((int64_t)k * nv + v) * ld;
-      raw[i] = codec.fetch2(X, idx + ea, idx + eb, va, vb, cs);
+    for (int i = 0; i < kPer; ++i) {
+      const int k = warp + i * kWarps;
+      if (k < ns) {
+        const int64_t idx = ((int64_t)k * nv + v) * ld;
+        raw[i] = codec.fetch2(X, idx + ea, idx + eb, va, vb, cs);
+      }
     }
-  }
 #pragma unroll
-  for (int i = 0; i < kPer; ++i) {
-    const int k = warp + i * kWarps;
-    if (k < ns) {
-      float2 X0, Y0, Z0;
-      codec.decode_raw(raw[i], X0, Y0, Z0);
-      float *s = sx + k * 3 * kTile;
-      s[lane] = X0.x;
-      s[lane + 32] = X0.y;
-      s[kTile + lane] = Y0.x;
-      s[kTile + lane + 32] = Y0.y;
-      s[2 * kTile + lane] = Z0.x;
-      s[2 * kTile + lane + 32] = Z0.y;
+    for (int i = 0; i < kPer; ++i) {
+      const int k = warp + i * kWarps;
+      if (k < ns) {
+        float2 X0, Y0, Z0;
+        codec.decode_raw(raw[i], X0, Y0, Z0);
+        float *s = sx + k * 3 * kTile;
+        s[lane] = X0.x;
+        s[lane + 32] = X0.y;
+        s[kTile + lane] = Y0.x;
+        s[kTile + lane + 32] = Y0.y;
+        s[2 * kTile + lane] = Z0.x;
+        s[2 * kTile + lane + 32] = Z0.y;
+      }
     }
   }
 }
@@ -620,7 +617,8 @@ __device__ __forceinline__ void unpair(float2 X, float2 Y, float2 Z, float a[3],
   b[0] = X.y; b[1] = Y.y; b[2] = Z.y;
 }
 
-// Step 9: F^s rows from q^s, grad w^s rows, metric rows S and |J|.
+// Step 9: F^s rows from q^s, grad w^s rows, metric rows S and |J| (FP32 rows;
+// compressed rows run k_fr_flux_w).
 template <class C>
 __global__ void __launch_bounds__(kThreads) k_fr_flux(const __grid_constant__ DevFormat F,
                                                       FrGasDev gas, FrSmem L, int ns,
@@ -678,7 +676,7 @@ __device__ __forceinline__ int64_t neighbour(int64_t e, int c, int s, int Ex, in
   return (iz * Ey + iy) * Ex + ix;
 }
 
-// Viscous flux rows of one side from its fetched inputs.
+// Viscous flux rows of one side from its fetched inputs (FP32 rows).
 template <class C>
 __device__ __forceinline__ void side_viscous_from(const C &codec, const PointIn<C> &in,
                                                   const FrGasDev &gas, float Fa[4][3],
@@ -706,9 +704,10 @@ __device__ __forceinline__ void side_viscous_from(const C &codec, const PointIn<
 // evaluated once: the thread of flux point f on the + face of axis c of
 // element e also writes the matching point f - q^2 on the - face of the
 // neighbour e' across it (a bijection on a periodic mesh, so every output has
-// one writer), and each side's rows are decoded once.
+// one writer), and each side's rows are read once.  FP32 rows; compressed
+// rows run k_fr_commonvis_w.
 template <class C>
-__global__ void __launch_bounds__(kThreads, C::kInterfaceBlocks) k_fr_commonvis(
+__global__ void __launch_bounds__(kThreads, 1) k_fr_commonvis(
     const __grid_constant__ DevFormat F, FrGasDev gas, FrSmem L, int q, int Ex, int Ey, int Ez,
     const typename C::T *G, const typename C::T *nrm, const typename C::T *S,
     const float *__restrict__ detJ, const float *__restrict__ qf, const float *__restrict__ nFinv,
