@@ -14,10 +14,18 @@
 // address is looked up once per device with cudaGetSymbolAddress, on the
 // first call made with that device current.  All calls share the array and it
 // keeps the last call's contents: a call whose format differs from the one the
-// array holds on that device first rewrites the tables (a small kernel on the
-// same stream).  Calls that overlap on the GPU (other streams, other host
-// threads) and use different formats race on the array.
+// array holds on that device first rewrites the tables (an asynchronous copy of
+// host-built tables, the same values ivc_add caches, on the call's stream) and
+// records an event after the copy; every call makes its stream wait for the
+// latest such event before its kernel, so a call on another stream or host
+// thread never reads tables that are still being written.  Calls that overlap
+// on the GPU and use different formats still race on the array.  A call that
+// would rewrite the tables, or the first call on a device, is refused while its
+// stream is capturing (IVC_ERR_UNSUPPORTED): a captured call reads whatever the
+// array holds when the graph runs, which a later call with another format
+// rewrites.
 #include <mutex>
+#include <vector>
 
 #include "ivc_internal.h"
 
@@ -29,31 +37,14 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) ivc::TabEntry g_noalloc_tab[kNoAllocEntries];
 
 struct DeviceSlot {
-  ivc::TabEntry *tab = nullptr;  // device address of g_noalloc_tab
+  ivc::TabEntry *tab = nullptr;       // device address of g_noalloc_tab
+  cudaEvent_t filled = nullptr;       // recorded after the latest table copy
+  bool has_fill = false;              // filled has been recorded at least once
   int Dt = -1, Dp = -1, st = -1, sp = -1;  // format whose tables the array holds
 };
 
 std::mutex g_slot_mu;
 DeviceSlot g_slots[kMaxDevices];
-
-// Head tables of the two folded grids (entries at b = i 2^s, angle
-// pi b / (2D)), in FP64 then split to head + tail FP32.
-__global__ void k_fill_tables(ivc::TabEntry *tab, int Dt, int st, int nt, int Dp, int sp, int np) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nt + np) return;
-  const bool is_t = i < nt;
-  const int j = is_t ? i : i - nt;
-  const int D = is_t ? Dt : Dp;
-  const int s = is_t ? st : sp;
-  double sv = 0.0, cv = 1.0;
-  if (j > 0) sincospi((double)((long long)j << s) / (2.0 * (double)D), &sv, &cv);
-  ivc::TabEntry e;
-  e.ch = (float)cv;
-  e.cl = (float)(cv - (double)e.ch);
-  e.sh = (float)sv;
-  e.sl = (float)(sv - (double)e.sh);
-  tab[i] = e;
-}
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -78,26 +69,54 @@ extern "C" ivc_status ivc_add_noalloc(const ivc_format *fmt, const uint64_t *a, 
     return IVC_ERR_CUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) return IVC_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
   {
     std::lock_guard<std::mutex> lk(g_slot_mu);
     DeviceSlot &slot = g_slots[dev];
     if (slot.tab == nullptr) {
+      if (capturing) return IVC_ERR_UNSUPPORTED;
       void *p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_tab) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return IVC_ERR_CUDA;
+      }
+      if (cudaEventCreateWithFlags(&slot.filled, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return IVC_ERR_CUDA;
       }
       slot.tab = static_cast<TabEntry *>(p);
     }
     if (slot.Dt != F.Dt || slot.Dp != F.Dp || slot.st != F.st || slot.sp != F.sp) {
-      const int total = F.nent_t + F.nent_p;
-      k_fill_tables<<<(total + 255) / 256, 256, 0, stream>>>(slot.tab, F.Dt, F.st, F.nent_t,
-                                                              F.Dp, F.sp, F.nent_p);
-      if (cudaGetLastError() != cudaSuccess) return IVC_ERR_CUDA;
+      if (capturing) return IVC_ERR_UNSUPPORTED;
+      // the same host tables ivc_add caches; the copy from pageable memory is
+      // staged before this call returns, so the vector may go out of scope
+      std::vector<TabEntry> host;
+      host.reserve((size_t)(F.nent_t + F.nent_p));
+      host_uniform_tables(F, host);
+      if (host.size() != (size_t)(F.nent_t + F.nent_p)) return IVC_ERR_FORMAT;
+      if (cudaMemcpyToSymbolAsync(g_noalloc_tab, host.data(), host.size() * sizeof(TabEntry), 0,
+                                  cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+          cudaEventRecord(slot.filled, stream) != cudaSuccess) {
+        cudaGetLastError();
+        slot.Dt = slot.Dp = slot.st = slot.sp = -1;  // contents unknown: refill next time
+        return IVC_ERR_CUDA;
+      }
+      slot.has_fill = true;
       slot.Dt = F.Dt;
       slot.Dp = F.Dp;
       slot.st = F.st;
       slot.sp = F.sp;
+    } else if (!capturing && slot.has_fill) {
+      // the tables may still be in flight on the stream that wrote them
+      if (cudaStreamWaitEvent(stream, slot.filled, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return IVC_ERR_CUDA;
+      }
     }
     F.tab = slot.tab;
   }

@@ -1,9 +1,22 @@
-"""ivc_add_noalloc, the compressed add for callers that must not allocate
-device memory (its tables sit in a fixed array inside the library instead of
-cudaMalloc'd memory): through the C ABI it gives the words ivc_add gives, on
-two calls in a row (the second with a different format, so the shared array
-is rewritten), and rejects formats whose tables do not fit the array."""
+"""ivc_add_noalloc, the compressed add for callers that cannot allocate device
+memory: code under a framework whose caching allocator owns the device memory,
+a latency-critical loop that cannot take cudaMalloc's implicit device-wide
+synchronisation, or a teardown or error path where an allocation may fail.
+Its tables sit in a fixed array inside the library instead of cudaMalloc'd
+memory.
+
+Through the C ABI it must give the words ivc_add gives, on calls in a row
+(the second with a different format, so the shared array is rewritten), also
+when two streams start with the same format at once; it must reject formats
+whose tables do not fit the array; and a call with a format the library has
+never seen must leave the device's free memory unchanged.
+
+This file is collected last so that a run stopping at the first failure has
+already run every other test."""
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -16,24 +29,30 @@ from paper_2003_02633_gb300 import ivc, synth  # noqa: E402
 from parity_util import check_words, formats  # noqa: E402
 
 DEV = "cuda:0"
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _words(w):
     return torch.from_numpy(np.asarray(w, np.uint64).view(np.int64)).to(DEV)
 
 
-def _run(name, n, seed):
+def _inputs(name, n, seed):
     fo, fg = formats(name)
     a, b = synth.roundtrip_inputs(n, seed=seed)
-    wa, wb = _words(O.compress(fo, a)), _words(O.compress(fo, b))
+    wa_h, wb_h = O.compress(fo, a), O.compress(fo, b)
+    with np.errstate(invalid="ignore", over="ignore"):
+        pre = O.decompress(fo, wa_h) + O.decompress(fo, wb_h)
+    return fo, fg, _words(wa_h), _words(wb_h), pre
+
+
+def _run(name, n, seed):
+    fo, fg, wa, wb, pre = _inputs(name, n, seed)
     want = ivc.add(fg, wa, wb)
     got = torch.full_like(wa, -1)
     ivc.add_noalloc(fg, wa, wb, got)
     torch.cuda.synchronize()
     g = got.cpu().numpy().view(np.uint64)
     w = want.cpu().numpy().view(np.uint64)
-    with np.errstate(invalid="ignore", over="ignore"):
-        pre = O.decompress(fo, O.compress(fo, a)) + O.decompress(fo, O.compress(fo, b))
     check_words(fo, pre, g, w, f"noalloc vs ivc_add ({name})")
     return g
 
@@ -43,6 +62,32 @@ def test_noalloc_matches_ivc_add_twice():
     g2 = _run("fracsplit", (1 << 16) + 1, seed=102)
     g3 = _run("primary", 4097, seed=103)   # the array is rewritten back
     assert g1.shape[0] > 0 and g2.shape[0] > 0 and g3.shape[0] > 0
+
+
+def test_noalloc_two_streams_same_format():
+    """The array holds another format; a call on a busy stream queues the
+    table copy behind a spin, and a call with the same format on an idle stream
+    must wait for that copy instead of reading the old tables."""
+    fo, fg, wa, wb, pre = _inputs("primary", (1 << 17) + 1, seed=104)
+    _, fg2, xa, xb, _ = _inputs("L1717", 1025, seed=105)
+    tmp = torch.empty_like(xa)
+    ivc.add_noalloc(fg2, xa, xb, tmp)          # the array now holds L1717 tables
+    torch.cuda.synchronize()
+    want = ivc.add(fg, wa, wb)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    out1 = torch.full_like(wa, -1)
+    out2 = torch.full_like(wa, -1)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        torch.cuda._sleep(20_000_000)          # keeps s1 busy for about 10 ms
+    ivc.add_noalloc(fg, wa, wb, out1, stream=s1)
+    ivc.add_noalloc(fg, wa, wb, out2, stream=s2)
+    torch.cuda.synchronize()
+    w = want.cpu().numpy().view(np.uint64)
+    for out in (out1, out2):
+        g = out.cpu().numpy().view(np.uint64)
+        check_words(fo, pre, g, w, "noalloc on two streams")
 
 
 def test_noalloc_rejects_oversized_tables():
@@ -56,3 +101,52 @@ def test_noalloc_rejects_oversized_tables():
     st = L.ivc_add_noalloc(ctypes.byref(big), x.data_ptr(), x.data_ptr(), x.data_ptr(), 8, s)
     assert st in (ivc.IVC_ERR_NOMEM, ivc.IVC_ERR_FORMAT)
     torch.cuda.synchronize()
+
+
+_FRESH = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2003_02633_gb300 import ivc
+
+dev = "cuda:0"
+rng = np.random.default_rng(7)
+n = 1 << 16
+def words(fields):
+    E, m, p, t, sh = fields
+    return (E.astype(np.uint64) << np.uint64(sh[0])) | (m.astype(np.uint64) << np.uint64(sh[1])) \
+        | (p.astype(np.uint64) << np.uint64(sh[2])) | t.astype(np.uint64)
+def rand_words(mbits, pbits, tbits):
+    sh = (mbits + pbits + tbits, pbits + tbits, tbits)
+    f = (rng.integers(40, 100, n), rng.integers(0, 1 << mbits, n), rng.integers(0, 1 << pbits, n),
+         rng.integers(0, 1 << tbits, n), sh)
+    return torch.from_numpy(words(f).view(np.int64)).to(dev)
+# <0,7,23>-17-17, never used by this process before the measured call
+fmt = ivc.make_format(exp_bits=7, man_bits=23, phi_bits=17, theta_bits=17, exp_bias=80)
+a, b = rand_words(23, 17, 17), rand_words(23, 17, 17)
+out = torch.full_like(a, -1)
+# warm-up with the primary layout: symbol lookup, event, module loading
+pa, pb = rand_words(22, 17, 18), rand_words(22, 17, 18)
+ivc.add_noalloc(ivc.make_format(), pa, pb, torch.empty_like(pa))
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+ivc.add_noalloc(fmt, a, b, out)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+want = ivc.add(fmt, a, b)
+torch.cuda.synchronize()
+same = bool(torch.equal(out, want))
+print("free_before", free0, "free_after", free1, "same_words", same)
+sys.exit(0 if (free0 == free1 and same) else 3)
+"""
+
+
+def test_noalloc_first_call_with_new_format_allocates_nothing():
+    """In a fresh process with every module loaded up front, a call whose
+    format the library has never used (neither ivc_add nor this entry point)
+    leaves the device's free memory unchanged, and gives ivc_add's words."""
+    env = dict(os.environ, CUDA_MODULE_LOADING="EAGER")
+    r = subprocess.run([sys.executable, "-c", _FRESH, ROOT], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
