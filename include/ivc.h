@@ -120,18 +120,41 @@ ivc_status ivc_decompress(const ivc_format *fmt, const uint64_t *w, int64_t n,
                           float *xyz, ivc_layout layout, int64_t ld,
                           ivc_stream_t stream);
 
+/* The same words as ivc_compress and the same vectors as ivc_decompress
+ * (AoS layout only), with every rounding decision of Sec. 2.1 / Eq. a_disc
+ * (angle bins), Sec. 2.3 (the RN32 magnitude) and Eq. a_inv (the decoded
+ * components) taken by the exact-decision path in 64/128-bit integer
+ * arithmetic that the fast kernels use only near a boundary: integer Taylor
+ * series for cos/sin (about 2^-57 relative) and an exact norm decision.  No
+ * floating point wider than FP32.  Slower; meant for validating results.
+ * Arguments, ownership and errors as ivc_compress / ivc_decompress. */
+ivc_status ivc_compress_exact(const ivc_format *fmt, const float *xyz, int64_t n, uint64_t *w,
+                              ivc_counts *counts, ivc_stream_t stream);
+ivc_status ivc_decompress_exact(const ivc_format *fmt, const uint64_t *w, int64_t n, float *xyz,
+                                ivc_stream_t stream);
+
 /* Sec. 5: c[i] = compress(decompress(a[i]) + decompress(b[i])), FP32 adds. */
 ivc_status ivc_add(const ivc_format *fmt, const uint64_t *a, const uint64_t *b,
                    uint64_t *c, int64_t n, ivc_stream_t stream);
 
-/* y[i] = compress(fmaf(alpha, decompress(x[i]), decompress(y[i]))). */
+/* y[i] = compress(fmaf(alpha, decompress(x[i]), decompress(y[i]))).
+ * The paper's Sec. 5 kernel (decompress both operands, combine in FP32,
+ * compress the result) with the combination y + alpha x in place of a + b,
+ * one fused multiply-add per component (single rounding).  In place: y is
+ * read and written.  Words: device, 8-byte aligned (16 for the two-per-thread
+ * kernel).  Errors and results as ivc_add. */
 ivc_status ivc_axpy(const ivc_format *fmt, float alpha, const uint64_t *x,
                     uint64_t *y, int64_t n, ivc_stream_t stream);
 
 /* Pointwise update of a compressed field (velocity v, forcing f):
  * v_new = fmaf(dt, decompress(f[i]), decompress(v[i]));
  * v_out[i] = compress(v_new); if rho and m_out are both non-NULL,
- * m_out[i] = compress(rho[i] * v_new) (FP32 products).  rho: device FP32. */
+ * m_out[i] = compress(rho[i] * v_new) (FP32 products).  rho: device FP32.
+ * The Sec. 5 pattern (decompress, FP32 arithmetic, recompress) applied to the
+ * flow variables the paper compresses in its test cases: the velocity and
+ * momentum 3-vectors of the Taylor-Green vortex of Sec. 4.2 (initial fields
+ * there), advanced by an explicit forcing step.  v_out may equal v (in place);
+ * m_out must not alias v, f or v_out.  Errors as ivc_add. */
 ivc_status ivc_pointwise_update(const ivc_format *fmt, float dt, const uint64_t *v,
                                 const uint64_t *f, const float *rho, uint64_t *v_out,
                                 uint64_t *m_out, int64_t n, ivc_stream_t stream);
@@ -173,7 +196,11 @@ ivc_status ivc_error_stats(const float *x, const float *xh, int64_t n, double *o
 
 /* ---------------------------------------------------------------------------
  * Batched form over many fields of uneven length (one persistent launch
- * driven by a device work list, replayed from a CUDA graph). */
+ * driven by a device work list, replayed from a CUDA graph).  There is no
+ * counterpart in the paper: it is a library-level way to run the Sec. 5 add
+ * and the axpy above over many fields at once (the fields of a
+ * multi-partition mesh, each with its own length), with results identical to
+ * one ivc_add / ivc_axpy call per field. */
 typedef enum { IVC_OP_ADD = 0, IVC_OP_AXPY = 1 } ivc_op;
 
 typedef struct {
@@ -214,7 +241,8 @@ ivc_status ivc_launch_plan_direct(ivc_plan plan, ivc_stream_t stream);
 ivc_status ivc_plan_status(ivc_plan plan, ivc_stream_t stream);
 ivc_status ivc_plan_destroy(ivc_plan plan);
 
-/* Times candidate launch shapes of `op` on the caller's buffers (n vectors;
+/* Launch-shape tuner (no counterpart in the paper; results do not depend on
+ * the shape).  Times candidate launch shapes of `op` on the caller's buffers (n vectors;
  * for IVC_OP_AXPY, b is used as the y operand and is overwritten; for
  * IVC_OP_ADD, c is overwritten) and writes the fastest to *best.  Runs
  * synchronously on `stream`. */
@@ -437,11 +465,17 @@ ivc_status ivc_release_tables(void);
  * first call on a device looks up that array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array and it keeps the last call's contents; a call
- * with a format whose tables are not the ones the array holds rewrites them
- * first on `stream`.  Calls that overlap on the GPU with different formats
- * race on the array.  Calls no cudaMalloc/cudaFree.  Errors: as ivc_add, plus
- * IVC_ERR_UNSUPPORTED for the tanh map and IVC_ERR_NOMEM for a format whose
- * tables exceed the array (more than 2048 entries). */
+ * with a format whose tables are not the ones the array holds first copies
+ * them (host-built, the values ivc_add uses) on `stream` and records an event;
+ * every later call on any stream waits for that event before its kernel.
+ * Calls that overlap on the GPU with different formats race on the array.
+ * While `stream` is capturing, the first call on a device and a call that
+ * would rewrite the tables return IVC_ERR_UNSUPPORTED; a captured call reads
+ * the array when the graph runs, so a later call with another format changes
+ * what a replay of that graph decodes with.  Calls no cudaMalloc/cudaFree.
+ * Errors: as ivc_add, plus IVC_ERR_UNSUPPORTED for the tanh map and
+ * IVC_ERR_NOMEM for a format whose tables exceed the array (more than 2048
+ * entries). */
 ivc_status ivc_add_noalloc(const ivc_format *fmt, const uint64_t *a, const uint64_t *b,
                            uint64_t *c, int64_t n, ivc_stream_t stream);
 

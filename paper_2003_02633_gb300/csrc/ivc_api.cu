@@ -194,6 +194,11 @@ ivc_status get_tables(const ivc_format *f, const Geometry &g, int device, TableS
 
 }  // namespace
 
+void ivc::host_uniform_tables(const DevFormat &F, std::vector<TabEntry> &out) {
+  uniform_table(F.Dt, out);
+  uniform_table(F.Dp, out);
+}
+
 // Fills every field of *F except the table pointers (no device work).
 ivc_status ivc::format_fields(const ivc_format *f, DevFormat *F, int *map_out) {
   Geometry g;
@@ -230,6 +235,8 @@ ivc_status ivc::format_fields(const ivc_format *f, DevFormat *F, int *map_out) {
   F->nent_p = table_entries(F->Dp, F->sp);
   ff_split(kPiL / (2.0L * F->Dt), F->Kt_h, F->Kt_l);
   ff_split(kPiL / (2.0L * F->Dp), F->Kp_h, F->Kp_l);
+  exact::pi_over_host(2LL * F->Dt, F->Kxt_m, F->Kxt_e);
+  exact::pi_over_host(2LL * F->Dp, F->Kxp_m, F->Kxp_e);
   F->tab = nullptr;
   {
     const unsigned __int128 two64 = (unsigned __int128)1 << 64;
@@ -406,6 +413,34 @@ ivc_status ivc_decompress(const ivc_format *fmt, const uint64_t *w, int64_t n, f
   }
   const LaunchShape s = default_shape(map, K_DECOMPRESS, F, n, 0, nullptr);
   return cuda_status(launch_decompress(map, F, w, n, xyz, layout, ld, s, stream));
+}
+
+ivc_status ivc_compress_exact(const ivc_format *fmt, const float *xyz, int64_t n, uint64_t *w,
+                              ivc_counts *counts, ivc_stream_t stream) {
+  if (n < 0) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!xyz || !w) return IVC_ERR_ARG;
+  if (!aligned(xyz, 4) || !aligned(w, 8) || (counts && !aligned(counts, 8))) return IVC_ERR_ALIGN;
+  const LaunchShape s = default_shape(map, K_COMPRESS, F, n, 0, nullptr);
+  return cuda_status(launch_compress_exact(map, F, xyz, n, w, counts, s, stream));
+}
+
+ivc_status ivc_decompress_exact(const ivc_format *fmt, const uint64_t *w, int64_t n, float *xyz,
+                                ivc_stream_t stream) {
+  if (n < 0) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  if (n == 0) return IVC_OK;
+  if (!xyz || !w) return IVC_ERR_ARG;
+  if (!aligned(xyz, 4) || !aligned(w, 8)) return IVC_ERR_ALIGN;
+  const LaunchShape s = default_shape(map, K_DECOMPRESS, F, n, 0, nullptr);
+  return cuda_status(launch_decompress_exact(map, F, w, n, xyz, s, stream));
 }
 
 ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t *b, uint64_t *c,

@@ -57,7 +57,7 @@ namespace fast {
 
 // Pair decode for a consumer that only needs the decoded components to within
 // one unit in the last place (the FP32 products of Algorithm 1): the same
-// double-float evaluation of r^ cos(theta^) sin(phi^) ... as decode2, rounded
+// float-float evaluation of r^ cos(theta^) sin(phi^) ... as decode2, rounded
 // to nearest instead of away from zero, so it needs no ambiguity test and no
 // generic fallback except for non-finite words.  Within 1.5 units of the
 // last place of the canonical decoded value.

@@ -3,37 +3,41 @@
 //
 // Every rounding decision the method makes is taken in FP32 arithmetic with a
 // stated error bound; the rare inputs whose decision the bound does not
-// settle are re-evaluated in FP64 (noinline helpers, off the common path).
+// settle are decided again in 64/128-bit integer arithmetic (ivc_exact.cuh,
+// noinline helpers, off the common path).  No floating point wider than FP32.
 //
 // Encoding (Sec. 2.1, 2.3, 3).
-//   magnitude: RN32(|x|) from a double-float sum of squares and a
-//     double-float square root (error < 2^-44); within 2^-42 of an FP32
-//     rounding midpoint the norm is recomputed in FP64.  Exponent rebiased,
-//     mantissa truncated (Sec. 2.3).
+//   magnitude: RN32(|x|) from a float-float sum of squares and a
+//     float-float square root (error < 2^-44); within 2^-42 of an FP32
+//     rounding midpoint the exact sign of |x|^2 - m^2 at the midpoint m
+//     decides.  Exponent rebiased, mantissa truncated (Sec. 2.3).
 //   angles: n = nint(t) (Eq. a_disc).  An FP32 estimate of t, good to a few
 //     hundredths of a bin, names the one rounding boundary k + 1/2 that can
 //     matter; a side-of-boundary test of the input against that boundary's
 //     direction decides k or k + 1:
 //       theta: sign(y cos(theta_h) - x sin(theta_h)),
 //       phi:   sign(rho cos(phi_h) - z sin(phi_h)),  rho = sqrt(x^2 + y^2),
-//     with cos/sin of the boundary in double-float (about 2^-42 relative) and
-//     error-free products; |test| below 2^-40 of its terms -> FP64 test.
+//     with cos/sin of the boundary in float-float (about 2^-42 relative) and
+//     error-free products; |test| below 2^-40 of its terms -> the test again
+//     with cos/sin to about 2^-57 (integer Taylor series).
 //     Exact ties (theta = 0, phi = pi/2) give a test value of exactly zero and
 //     round up.
 //
 // Decoding (Eq. a_inv, Eq. cart2sphere).  theta^ = pi (2 n_theta - N) / N and
 // phi^ = pi (2 n_phi) / (2M) are rational multiples of pi.  Each angle pi m / D
 // is folded exactly, in integers, onto [0, pi/4]; cos and sin there come from
-// a shared-memory table of double-float values at multiples of 2^s units
+// a shared-memory table of float-float values at multiples of 2^s units
 // (pi / (2D) each; at most 1024 entries) plus a Taylor step for the signed
 // remainder.
-// The products r cos(theta) sin(phi) etc. are formed in double-float and
+// The products r cos(theta) sin(phi) etc. are formed in float-float and
 // rounded away from zero with a directed-rounding FMA; when the value lies
 // within 2^-40 (relative) of an FP32 grid point the vector is decoded again
-// in FP64.
+// with cos/sin and products to about 2^-56 (integer arithmetic).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "ivc_exact.cuh"
 
 namespace ivc {
 
@@ -72,7 +76,9 @@ struct DevFormat {
   int32_t Dt, Dp;                   // theta grid pi m / N, phi grid pi m / (2M)
   int32_t nent_t, nent_p;           // table entries
   int32_t st, sp;                   // table step 2^s units
-  float Kt_h, Kt_l, Kp_h, Kp_l;     // pi / (2 D) in double-float
+  float Kt_h, Kt_l, Kp_h, Kp_l;     // pi / (2 D) in float-float
+  uint64_t Kxt_m, Kxp_m;            // pi / (2 D) = Kx_m 2^Kx_e (64-bit, exact paths)
+  int32_t Kxt_e, Kxp_e;
   const TabEntry *tab;              // global, nent_t + nent_p entries
   uint64_t div_magic;               // ceil(2^64 / (N + 1)) for the split
   // tanh companding
@@ -112,7 +118,7 @@ __device__ __forceinline__ void sincos_folded(int b, const TabEntry *__restrict_
   const int h = (s > 0) ? ((b + (1 << (s - 1))) >> s) : b;
   const float lf = (float)(b - (h << s));
   const TabEntry e = tab[h];
-  // beta = l pi / (2D) in double-float
+  // beta = l pi / (2D) in float-float
   const float bh = lf * Kh;
   const float bl = fmaf(lf, Kh, -bh) + lf * Kl;
   const float b2 = bh * bh;
@@ -155,22 +161,11 @@ __device__ __forceinline__ void sincospi_grid(int m, int D, const TabEntry *__re
   sn = f.swap ? cc : ss;
 }
 
-// FP64 cos and sin of pi m / D (signed), from the exact fold.
-static __device__ __noinline__ void sincospi_grid_f64(int m, int D, double &c, double &s) {
-  const Fold f = fold_grid(m, D);
-  double sb, cb;
-  sincospi((double)f.b / (2.0 * (double)D), &sb, &cb);
-  const double cc = f.swap ? sb : cb;
-  const double ss = f.swap ? cb : sb;
-  c = f.cneg ? -cc : cc;
-  s = f.sneg ? -ss : ss;
-}
-
 __device__ __forceinline__ FF neg_if(FF v, bool n) {
   return n ? FF{-v.h, -v.l} : v;
 }
 
-// Side test a c - b s for exact FP32 a (+ tail a_l), b and double-float c, s.
+// Side test a c - b s for exact FP32 a (+ tail a_l), b and float-float c, s.
 // Returns +1 / 0 (for "< 0") when settled, -1 when |value| is within the
 // error bound.
 __device__ __forceinline__ int side_ge(float a, float a_l, FF c, float b, FF s) {
@@ -189,7 +184,7 @@ __device__ __forceinline__ int side_ge(float a, float a_l, FF c, float b, FF s) 
   return d >= 0.0f ? 1 : 0;
 }
 
-// Round-up of r * (a * b) for non-negative double-floats a, b; sets amb when
+// Round-up of r * (a * b) for non-negative float-floats a, b; sets amb when
 // the value lies within the decode error bound of an FP32 grid point.
 __device__ __forceinline__ float ru_prod3(float r, FF a, FF b, bool &amb) {
   const float P = a.h * b.h;
@@ -214,12 +209,6 @@ __device__ __forceinline__ float ru_prod2(float r, FF a, bool &amb) {
 
 __device__ __forceinline__ float apply_sign(float mag, bool neg) {
   return (neg && mag != 0.0f) ? -mag : mag;
-}
-
-// Round a real value (FP64) away from zero to FP32; exact zero -> +0.
-__device__ __forceinline__ float ra32_f64(double v) {
-  if (v == 0.0) return 0.0f;
-  return v > 0.0 ? __double2float_ru(v) : __double2float_rd(v);
 }
 
 // --------------------------------------------------------------------------
@@ -254,30 +243,37 @@ __device__ __forceinline__ float magnitude_of(uint32_t E, uint32_t mant, const D
 // --------------------------------------------------------------------------
 // Decode one word (Eq. a_inv, Eq. cart2sphere).
 
-// FP64 decode of a finite word (the fallback of decode_word).
+// Exact-path decode of a finite word (the fallback of decode_word): cos/sin
+// and the products to about 2^-56 in integer arithmetic, rounded away from
+// zero.
 template <int MAP>
-static __device__ __noinline__ float3 decode_word_f64(uint64_t w, const DevFormat &F) {
+static __device__ __noinline__ float3 decode_word_exact(uint64_t w, const DevFormat &F) {
+  using namespace exact;
   const uint32_t E = (uint32_t)(w >> F.sh_e) & F.mask_e;
   const uint32_t mant = (uint32_t)(w >> F.sh_m) & F.mask_m;
   int nt, np;
   unpack_angles<MAP>(w, F, nt, np);
-  double ct, st, cp, sp;
+  SF ct, st, cp, sp;
+  bool ctn, stn, cpn, spn;
   if (MAP == MAP_TANH) {
     const TabEntry et = F.dec_t[nt];
     const TabEntry ep = F.dec_p[np];
-    ct = (double)et.ch + (double)et.cl;
-    st = (double)et.sh + (double)et.sl;
-    cp = (double)ep.ch + (double)ep.cl;
-    sp = (double)ep.sh + (double)ep.sl;
+    ct = sf_from_ff(et.ch, et.cl, ctn);
+    st = sf_from_ff(et.sh, et.sl, stn);
+    cp = sf_from_ff(ep.ch, ep.cl, cpn);
+    sp = sf_from_ff(ep.sh, ep.sl, spn);
   } else {
-    sincospi_grid_f64(2 * nt - F.N, F.Dt, ct, st);
-    sincospi_grid_f64(2 * np, F.Dp, cp, sp);
+    sincospi_grid(2 * nt - F.N, F.Dt, SF{F.Kxt_m, F.Kxt_e, false}, ct, st, ctn, stn);
+    sincospi_grid(2 * np, F.Dp, SF{F.Kxp_m, F.Kxp_e, false}, cp, sp, cpn, spn);
   }
-  const double r = (double)magnitude_of(E, mant, F);
-  return make_float3(ra32_f64(r * ct * sp), ra32_f64(r * st * sp), ra32_f64(r * cp));
+  const SF r = sf_from_float(magnitude_of(E, mant, F));
+  const SF R = sf_mul(r, sp);
+  return make_float3(apply_sign(ra32(sf_mul(R, ct)), ctn), apply_sign(ra32(sf_mul(R, st)), stn),
+                     apply_sign(ra32(sf_mul(r, cp)), cpn));
 }
 
-template <int MAP>
+// EXACT: every finite word through decode_word_exact (validation entry points).
+template <int MAP, bool EXACT = false>
 __device__ __forceinline__ float3 decode_word(uint64_t w, const DevFormat &F,
                                               const TabEntry *__restrict__ tab_t,
                                               const TabEntry *__restrict__ tab_p) {
@@ -308,12 +304,13 @@ __device__ __forceinline__ float3 decode_word(uint64_t w, const DevFormat &F,
     const float z = (cp.h != 0.0f) ? inf : 0.0f;
     return make_float3(apply_sign(x, ctn), apply_sign(y, stn), apply_sign(z, cpn));
   }
+  if (EXACT) return decode_word_exact<MAP>(w, F);
   const float r = magnitude_of(E, mant, F);
   bool amb = false;
   const float x = ru_prod3(r, ct, sp, amb);
   const float y = ru_prod3(r, st, sp, amb);
   const float z = ru_prod2(r, cp, amb);
-  if (amb) return decode_word_f64<MAP>(w, F);
+  if (amb) return decode_word_exact<MAP>(w, F);
   return make_float3(apply_sign(x, ctn), apply_sign(y, stn), apply_sign(z, cpn));
 }
 
@@ -325,40 +322,56 @@ __device__ __forceinline__ float pow2f(int e) {  // 2^e for e in [-126, 127]
   return __uint_as_float((uint32_t)(e + 127) << 23);
 }
 
-static __device__ __noinline__ float norm_rn_f64(float xs, float ys, float zs) {
-  const double s = (double)xs * xs + (double)ys * ys + (double)zs * zs;
-  return __double2float_rn(sqrt(s));
+// RN32 of the norm of the scaled vector, decided exactly (the fallback of the
+// float-float norm; r32 is its candidate).
+static __device__ __noinline__ float norm_rn_exact(float xs, float ys, float zs, float r32) {
+  return exact::norm_rn(xs, ys, zs, r32);
 }
 
+// Exact-path side tests (the fallbacks of side_ge): 1 when the input lies on
+// or above boundary k + 1/2, else 0.
+// theta: sign(y cos(t_b) - x sin(t_b)) >= 0.
 template <int MAP>
-static __device__ __noinline__ int side_theta_f64(float xs, float ys, int k, const DevFormat &F) {
-  double c, s;
+static __device__ __noinline__ int side_theta_exact(float xs, float ys, int k, const DevFormat &F) {
+  using namespace exact;
+  SF c, s;
+  bool cn, sn;
   if (MAP == MAP_TANH) {
     const TabEntry e = F.bnd_t[k];
-    c = (double)e.ch + (double)e.cl;
-    s = (double)e.sh + (double)e.sl;
+    c = sf_from_ff(e.ch, e.cl, cn);
+    s = sf_from_ff(e.sh, e.sl, sn);
   } else {
-    sincospi_grid_f64(2 * k + 1 - F.N, F.Dt, c, s);
+    sincospi_grid(2 * k + 1 - F.N, F.Dt, SF{F.Kxt_m, F.Kxt_e, false}, c, s, cn, sn);
   }
-  return ((double)ys * c - (double)xs * s) >= 0.0 ? 1 : 0;
+  const SF A = sf_mul(sf_from_float(ys), c);
+  const SF B = sf_mul(sf_from_float(xs), s);
+  return side_of(A, signbit(ys) != cn, B, signbit(xs) != sn);
 }
 
+// phi: sign(rho cos(p_b) - z sin(p_b)) >= 0 with rho = sqrt(x^2 + y^2) >= 0;
+// the magnitudes rho |cos| and |z| sin are compared through their squares.
 template <int MAP>
-static __device__ __noinline__ int side_phi_f64(float xs, float ys, float zs, int k,
-                                         const DevFormat &F) {
-  double c, s;
+static __device__ __noinline__ int side_phi_exact(float xs, float ys, float zs, int k,
+                                                  const DevFormat &F) {
+  using namespace exact;
+  SF c, s;
+  bool cn, sn;
   if (MAP == MAP_TANH) {
     const TabEntry e = F.bnd_p[k];
-    c = (double)e.ch + (double)e.cl;
-    s = (double)e.sh + (double)e.sl;
+    c = sf_from_ff(e.ch, e.cl, cn);
+    s = sf_from_ff(e.sh, e.sl, sn);
   } else {
-    sincospi_grid_f64(2 * k + 1, F.Dp, c, s);
+    sincospi_grid(2 * k + 1, F.Dp, SF{F.Kxp_m, F.Kxp_e, false}, c, s, cn, sn);
   }
-  const double rho = sqrt((double)xs * xs + (double)ys * ys);
-  return (rho * c - (double)zs * s) >= 0.0 ? 1 : 0;
+  const SF X = sf_from_float(xs), Y = sf_from_float(ys), Z = sf_from_float(zs);
+  const SF rho2 = sf_add(sf_mul(X, X), sf_mul(Y, Y));
+  const SF A2 = sf_mul(rho2, sf_mul(c, c));
+  const SF B2 = sf_mul(sf_mul(Z, Z), sf_mul(s, s));
+  return side_of(A2, cn, B2, signbit(zs) != sn);
 }
 
-template <int MAP>
+// EXACT: every decision through the exact helpers (validation entry points).
+template <int MAP, bool EXACT = false>
 __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const DevFormat &F,
                                                const TabEntry *__restrict__ tab_t,
                                                const TabEntry *__restrict__ tab_p,
@@ -392,7 +405,7 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
     const float s1 = pow2f(S1), s2 = pow2f(S2);
     xs = (x * s1) * s2; ys = (y * s1) * s2; zs = (z * s1) * s2;
   }
-  // Sum of squares in double-float.
+  // Sum of squares in float-float.
   const float px = xs * xs, ex_ = fmaf(xs, xs, -px);
   const float py = ys * ys, ey = fmaf(ys, ys, -py);
   const float pz = zs * zs, ez = fmaf(zs, zs, -pz);
@@ -402,7 +415,7 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
   float sh = r2h + pz;
   t = sh - r2h;
   const float sl = ((r2h - (sh - t)) + (pz - t)) + (r2l + ez);
-  // Double-float square root and RN32 of it.
+  // Float-float square root and RN32 of it.
   const float y0 = rsqrtf(sh);
   const float hy0 = 0.5f * y0;
   const float r0 = sh * y0;
@@ -414,8 +427,8 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
     const float half_ulp = __uint_as_float((__float_as_uint(r32) & 0x7f800000u) - (24u << 23));
     const float dev = fabsf((rh - r32) + rl);
     // a power of two has its lower midpoint a quarter ulp away: re-check those too
-    if (half_ulp - dev <= kNormAmbig * r32 || (__float_as_uint(r32) & 0x7fffffu) == 0u)
-      r32 = norm_rn_f64(xs, ys, zs);
+    if (EXACT || half_ulp - dev <= kNormAmbig * r32 || (__float_as_uint(r32) & 0x7fffffu) == 0u)
+      r32 = norm_rn_exact(xs, ys, zs, r32);
   }
   const uint32_t rb = __float_as_uint(r32);
   const int E8 = (int)(rb >> 23) - S;
@@ -447,11 +460,11 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
       c = neg_if(c, cn);
       s = neg_if(s, sn);
     }
-    int side = side_ge(ys, 0.0f, c, xs, s);
-    if (side < 0) side = side_theta_f64<MAP>(xs, ys, k, F);
+    int side = EXACT ? -1 : side_ge(ys, 0.0f, c, xs, s);
+    if (side < 0) side = side_theta_exact<MAP>(xs, ys, k, F);
     nt = k + side;
   }
-  // phi: rho = sqrt(x^2 + y^2) in double-float.
+  // phi: rho = sqrt(x^2 + y^2) in float-float.
   {
     float rho_h = 0.0f, rho_l = 0.0f;
     if (r2h > 0.0f) {
@@ -480,8 +493,8 @@ __device__ __forceinline__ uint64_t encode_vec(float x, float y, float z, const 
       sincospi_grid(2 * k + 1, F.Dp, tab_p, F.sp, F.Kp_h, F.Kp_l, c, s, cn, sn);
       c = neg_if(c, cn);
     }
-    int side = side_ge(rho_h, rho_l, c, zs, s);
-    if (side < 0) side = side_phi_f64<MAP>(xs, ys, zs, k, F);
+    int side = EXACT ? -1 : side_ge(rho_h, rho_l, c, zs, s);
+    if (side < 0) side = side_phi_exact<MAP>(xs, ys, zs, k, F);
     np = k + side;
   }
   if (nt == F.N) nt = 0;

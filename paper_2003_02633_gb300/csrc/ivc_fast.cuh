@@ -1,14 +1,14 @@
 // Fast path for the paper's primary layout <0,7,22>-17-18, b7 = 80 (Sec. 3,
 // Sec. 5), and for its fractional split at n_phi_max + 1 = floor(2^17.5)
 // (Sec. 2.4), default range handling.  Same results as the generic
-// path in ivc_device.cuh (shared tables, same error bounds, same FP64
-// fallbacks); organised for GB300 issue throughput:
+// path in ivc_device.cuh (shared tables, same error bounds, same exact
+// integer fallbacks); organised for GB300 issue throughput:
 //   * every thread carries two vectors and does their FP32 arithmetic with the
 //     packed f32x2 instructions (__ffma2 / __fadd2 / __fmul2, sm_100+);
 //   * field extraction, the exact angle folds and table addressing use float
 //     arithmetic on exact small integers and magic-number rounding, keeping
 //     the integer/compare pipe for the few decisions that need it;
-//   * encoding estimates t with a double-float octant-reduced atan (error
+//   * encoding estimates t with a float-float octant-reduced atan (error
 //     below 0.0035 bin in t) and runs the error-free side-of-boundary test only
 //     for coordinates within kEps of a rounding boundary, deferred to a
 //     per-warp queue;
@@ -35,6 +35,9 @@ struct GeoPrimary {
   static constexpr int N = 262143, M = 131071;
   static constexpr int ST = 8, SP = 8, NT = 513, NP = 513;
   static constexpr int MAP = MAP_UNIFORM;
+  // bin scales N / (2 pi) and M / pi as float-float head + tail
+  static constexpr float CTH = 0x1.45f2b6p+15f, CTL = -0x1.404a5ep-10f;
+  static constexpr float CPH = 0x1.45f264p+15f, CPL = -0x1.ce6e62p-13f;
   static constexpr uint32_t EALL = 127u;   // non-finite exponent field
   __device__ static uint32_t efield(uint32_t hi) { return hi >> 25; }
   __device__ static float mag(uint32_t hi) {
@@ -58,6 +61,9 @@ struct GeoSplit {
   static constexpr int N = 185363, M = 185362;
   static constexpr int ST = 7, SP = 8, NT = 725, NP = 725;
   static constexpr int MAP = MAP_FRACSPLIT;
+  // bin scales N / (2 pi) and M / pi as float-float head + tail
+  static constexpr float CTH = 0x1.ccf5cp+14f, CTL = 0x1.c5b442p-13f;
+  static constexpr float CPH = 0x1.ccf51ep+15f, CPL = -0x1.8199ccp-10f;
   static constexpr uint32_t EALL = 127u;
   __device__ static uint32_t efield(uint32_t hi) { return hi >> 25; }
   __device__ static float mag(uint32_t hi) {
@@ -84,6 +90,9 @@ struct GeoL1717 {
   static constexpr int N = 131071, M = 131071;
   static constexpr int ST = 7, SP = 8, NT = 513, NP = 513;
   static constexpr int MAP = MAP_UNIFORM;
+  // bin scales N / (2 pi) and M / pi as float-float head + tail
+  static constexpr float CTH = 0x1.45f264p+14f, CTL = -0x1.ce6e62p-14f;
+  static constexpr float CPH = 0x1.45f264p+15f, CPL = -0x1.ce6e62p-13f;
   static constexpr uint32_t EALL = 127u;
   __device__ static uint32_t efield(uint32_t hi) { return hi >> 25; }
   __device__ static float mag(uint32_t hi) { return __uint_as_float((hi >> 2) + (47u << 23)); }
@@ -104,6 +113,9 @@ struct GeoL1617 {
   static constexpr int N = 131071, M = 65535;
   static constexpr int ST = 7, SP = 7, NT = 513, NP = 513;
   static constexpr int MAP = MAP_UNIFORM;
+  // bin scales N / (2 pi) and M / pi as float-float head + tail
+  static constexpr float CTH = 0x1.45f264p+14f, CTL = -0x1.ce6e62p-14f;
+  static constexpr float CPH = 0x1.45f1cp+14f, CPL = 0x1.d32b58p-11f;
   static constexpr uint32_t EALL = 255u;
   __device__ static uint32_t efield(uint32_t hi) { return hi >> 24; }
   __device__ static float mag(uint32_t hi) { return __uint_as_float(hi >> 1); }
@@ -256,7 +268,7 @@ __device__ __forceinline__ float2 ru_pair(float2 P, float2 T, bool &amb0, bool &
   return x1;
 }
 
-// RU(r (a.h + a.l)) with a double-float a: returns (P, T) with P + T the value.
+// RU(r (a.h + a.l)) with a float-float a: returns (P, T) with P + T the value.
 __device__ __forceinline__ void prod2(float2 r, FF2 a, float2 &P, float2 &T) {
   P = mul2(r, a.h);
   const float2 Pe = fma2(r, a.h, neg2(P));
@@ -351,7 +363,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 
 // beta = atan(mn / mx) in [0, pi/4] for 0 <= mn <= mx, as an unevaluated sum
 // bh + bl with |error| < 5e-8 rad:
-//   * q = mn / mx as a double-float qh + ql (Newton-refined reciprocal and the
+//   * q = mn / mx as a float-float qh + ql (Newton-refined reciprocal and the
 //     exact residual mn - mx qh);
 //   * atan(q) = q + q^3 R(q^2), R a degree-7 polynomial from a
 //     least-squares-minimax (Lawson) fit on [0, 1] (7.4e-9 in exact
@@ -380,7 +392,7 @@ __device__ __forceinline__ void atan_ratio2(float2 mn, float2 mx, float2 &bh, fl
 }
 
 // Bin coordinate t = K0 + s1 * C * beta (K0 a multiple of 1/4, s1 = +-1,
-// C = n_max / pi or n_max / (2 pi) in double-float), returned as floor and
+// C = n_max / pi or n_max / (2 pi) in float-float), returned as floor and
 // fraction computed without rounding the large sum: C beta = G + small
 // (exact products and TwoSum), G = Gi + Gf with Gi integral, then
 // t = [K0 + s1 Gi] + s1 (Gf + small).  Error below 0.002 bin.
@@ -443,16 +455,13 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
                                     (__float_as_uint(y.x) & 0x80000000u)),
                     __uint_as_float(__float_as_uint((u1 != v1) ? -1.0f : 1.0f) ^
                                     (__float_as_uint(y.y) & 0x80000000u)));
-    const BinCoord2 c = bin_coord2(add2(K0, bc(0.5f)), s1, bh, bl,
-                                   (float)((double)kN / 6.283185307179586),
-                                   (float)((double)kN / 6.283185307179586 -
-                                           (double)(float)((double)kN / 6.283185307179586)));
+    const BinCoord2 c = bin_coord2(add2(K0, bc(0.5f)), s1, bh, bl, G::CTH, G::CTL);
     e.fl_t = c.fl;
     e.fr_t = c.fr;
   }
   // phi = atan2(rho, z); t = K0 + s1 g, g = M beta / pi
   {
-    // rho = sqrt(x^2 + y^2): one Newton step on the double-float sum (relative
+    // rho = sqrt(x^2 + y^2): one Newton step on the float-float sum (relative
     // error 2^-24, 0.0012 bin); 0 stays about 1e-18
     const float2 rr = make_float2(fmaxf(r2h.x, 1e-36f), fmaxf(r2h.y, 1e-36f));
     const float2 yr = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
@@ -469,9 +478,7 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
     const float2 K0 = make_float2(u0 ? 0.5f * (float)kM : (n0 ? (float)kM : 0.0f),
                                   u1 ? 0.5f * (float)kM : (n1 ? (float)kM : 0.0f));
     const float2 s1 = make_float2((u0 != n0) ? -1.0f : 1.0f, (u1 != n1) ? -1.0f : 1.0f);
-    const BinCoord2 c = bin_coord2(K0, s1, bh, bl, (float)((double)kM / 3.141592653589793),
-                                   (float)((double)kM / 3.141592653589793 -
-                                           (double)(float)((double)kM / 3.141592653589793)));
+    const BinCoord2 c = bin_coord2(K0, s1, bh, bl, G::CPH, G::CPL);
     e.fl_p = c.fl;
     e.fr_p = c.fr;
   }
@@ -513,8 +520,8 @@ __device__ __forceinline__ int exact_side(int kind, int k, float xs, float ys, f
   }
   const int side = side_ge(a, a_l, c, ph ? zs : xs, s);
   if (side >= 0) return side;
-  return ph ? side_phi_f64<G::MAP>(xs, ys, zs, k, F)
-            : side_theta_f64<G::MAP>(xs, ys, k, F);
+  return ph ? side_phi_exact<G::MAP>(xs, ys, zs, k, F)
+            : side_theta_exact<G::MAP>(xs, ys, k, F);
 }
 
 template <int MAP>
@@ -557,7 +564,7 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
                            __float_as_uint(z.y) & 0x7fffffffu);
   const bool gen0 = !((am0 - 0x2F800000u) < 0x20000000u);
   const bool gen1 = !((am1 - 0x2F800000u) < 0x20000000u);
-  // squares and sums in double-float
+  // squares and sums in float-float
   const float2 px = mul2(x, x), ex = fma2(x, x, neg2(px));
   const float2 py = mul2(y, y), ey = fma2(y, y, neg2(py));
   const float2 pz = mul2(z, z), ez = fma2(z, z, neg2(pz));
@@ -567,7 +574,7 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   const float2 sh = add2(r2h, pz);
   t = sub2(sh, r2h);
   const float2 sl = add2(add2(sub2(r2h, sub2(sh, t)), sub2(pz, t)), add2(r2l, ez));
-  // double-float square root, RN32
+  // float-float square root, RN32
   const float2 y0 = make_float2(rsqrtf(sh.x), rsqrtf(sh.y));
   const float2 hy0 = mul2(y0, bc(0.5f));
   const float2 q0 = mul2(sh, y0);

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "../../include/ivc.h"
 #include "ivc_device.cuh"
@@ -67,6 +68,13 @@ cudaError_t launch_compress(int map, const DevFormat &F, const float *xyz, int l
 cudaError_t launch_decompress(int map, const DevFormat &F, const uint64_t *w, int64_t n,
                               float *xyz, int layout, int64_t ld, const LaunchShape &s,
                               cudaStream_t st);
+// The same with every rounding decision through the exact integer helpers
+// (AoS only; validation entry points).
+cudaError_t launch_compress_exact(int map, const DevFormat &F, const float *xyz, int64_t n,
+                                  uint64_t *w, ivc_counts *counts, const LaunchShape &s,
+                                  cudaStream_t st);
+cudaError_t launch_decompress_exact(int map, const DevFormat &F, const uint64_t *w, int64_t n,
+                                    float *xyz, const LaunchShape &s, cudaStream_t st);
 cudaError_t launch_add(int map, const DevFormat &F, const uint64_t *a, const uint64_t *b,
                        uint64_t *c, int64_t n, const LaunchShape &s, cudaStream_t st);
 cudaError_t launch_axpy(int map, const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
@@ -139,6 +147,11 @@ int occupancy(int map, int kind, int block, size_t smem);
 
 // Format fields without table pointers (host only, no device work).
 ivc_status format_fields(const ivc_format *f, DevFormat *F, int *map_out);
+
+// Host copies of the folded head tables of a uniform or fractional-split
+// format (theta grid, then phi grid: F.nent_t + F.nent_p entries), built by
+// the same code as the tables the library caches on the device.
+void host_uniform_tables(const DevFormat &F, std::vector<TabEntry> &out);
 
 // Launch shape: block size from cfg (default 256), grid = SMs x resident
 // blocks (capped by the work), tables in dynamic shared memory.

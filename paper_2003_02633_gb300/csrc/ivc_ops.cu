@@ -39,7 +39,8 @@ __device__ __forceinline__ void flush_counts(const Events &ev, ivc_counts *count
 
 // ------------------------------------------------------------------ compress
 
-template <int MAP>
+// EXACT: every rounding decision through the exact integer helpers.
+template <int MAP, bool EXACT = false>
 __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ DevFormat F,
                                                   const float *__restrict__ xyz, int layout,
                                                   int64_t ld, int64_t n, uint64_t *w,
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ DevFor
       z = __ldcs(xyz + 2 * ld + i);
     }
     __stcs(reinterpret_cast<unsigned long long *>(w) + i,
-           (unsigned long long)encode_vec<MAP>(x, y, z, F, tab_t, tab_p, flags));
+           (unsigned long long)encode_vec<MAP, EXACT>(x, y, z, F, tab_t, tab_p, flags));
     ev.add(flags);
   }
   flush_counts(ev, counts);
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ DevFor
 
 // ---------------------------------------------------------------- decompress
 
-template <int MAP>
+template <int MAP, bool EXACT = false>
 __global__ void __launch_bounds__(256) k_decompress(const __grid_constant__ DevFormat F,
                                                     const uint64_t *__restrict__ w, int64_t n,
                                                     float *xyz, int layout, int64_t ld) {
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(256) k_decompress(const __grid_constant__ DevF
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint64_t word = __ldcs(reinterpret_cast<const unsigned long long *>(w) + i);
-    const float3 v = decode_word<MAP>(word, F, tab_t, tab_p);
+    const float3 v = decode_word<MAP, EXACT>(word, F, tab_t, tab_p);
     if (layout == IVC_AOS) {
       __stcs(xyz + 3 * i, v.x);
       __stcs(xyz + 3 * i + 1, v.y);
@@ -258,7 +259,7 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
 }
 
 template <int OP, class G>
-__global__ void __launch_bounds__(256) k_fused_fast(const __grid_constant__ DevFormat F,
+__global__ void __launch_bounds__(256, 3) k_fused_fast(const __grid_constant__ DevFormat F,
                                                     const uint64_t *a, const uint64_t *b,
                                                     uint64_t *c, int64_t n, float alpha) {
   IVC_TABLES(F, G::MAP);
@@ -545,6 +546,41 @@ cudaError_t launch_decompress(int map, const DevFormat &F, const uint64_t *w, in
                               float *xyz, int layout, int64_t ld, const LaunchShape &s,
                               cudaStream_t st) {
   IVC_DISPATCH_MAP(map, k_decompress, F, w, n, xyz, layout, ld);
+}
+
+cudaError_t launch_compress_exact(int map, const DevFormat &F, const float *xyz, int64_t n,
+                                  uint64_t *w, ivc_counts *counts, const LaunchShape &s,
+                                  cudaStream_t st) {
+  switch (map) {
+    case MAP_UNIFORM:
+      k_compress<MAP_UNIFORM, true><<<s.grid, s.block, s.smem, st>>>(F, xyz, IVC_AOS, 0, n, w,
+                                                                     counts);
+      break;
+    case MAP_TANH:
+      k_compress<MAP_TANH, true><<<s.grid, s.block, s.smem, st>>>(F, xyz, IVC_AOS, 0, n, w, counts);
+      break;
+    default:
+      k_compress<MAP_FRACSPLIT, true><<<s.grid, s.block, s.smem, st>>>(F, xyz, IVC_AOS, 0, n, w,
+                                                                       counts);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decompress_exact(int map, const DevFormat &F, const uint64_t *w, int64_t n,
+                                    float *xyz, const LaunchShape &s, cudaStream_t st) {
+  switch (map) {
+    case MAP_UNIFORM:
+      k_decompress<MAP_UNIFORM, true><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz, IVC_AOS, 0);
+      break;
+    case MAP_TANH:
+      k_decompress<MAP_TANH, true><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz, IVC_AOS, 0);
+      break;
+    default:
+      k_decompress<MAP_FRACSPLIT, true><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz, IVC_AOS, 0);
+      break;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_add(int map, const DevFormat &F, const uint64_t *a, const uint64_t *b,

@@ -77,6 +77,8 @@ _SIGS = {
     "ivc_release_tables": [],
     "ivc_compress": [_FMT, _P, _I, _I64, _I64, _P, _P, _P],
     "ivc_decompress": [_FMT, _P, _I64, _P, _I, _I64, _P],
+    "ivc_compress_exact": [_FMT, _P, _I64, _P, _P, _P],
+    "ivc_decompress_exact": [_FMT, _P, _I64, _P, _P],
     "ivc_add": [_FMT, _P, _P, _P, _I64, _P],
     "ivc_add_cfg": [_FMT, _P, _P, _P, _I64, ctypes.POINTER(ivc_launch_config), _P],
     "ivc_axpy": [_FMT, _F, _P, _P, _I64, _P],
@@ -217,6 +219,30 @@ def decompress(fmt, w, out=None, stream=None):
         out = torch.empty((n, 3), dtype=torch.float32, device=w.device)
     _chk(load().ivc_decompress(ctypes.byref(fmt), _ptr(w), n, _ptr(out), IVC_AOS, 0,
                                _stream(stream)), "ivc_decompress")
+    return out
+
+
+def compress_exact(fmt, xyz, out=None, counts=None, stream=None):
+    """ivc_compress_exact: every rounding decision by the exact integer path
+    (AoS FP32 input of shape (n, 3))."""
+    import torch
+    n = xyz.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=xyz.device)
+    cp = _ptr(counts) if counts is not None else None
+    _chk(load().ivc_compress_exact(ctypes.byref(fmt), _ptr(xyz), n, _ptr(out), cp,
+                                   _stream(stream)), "ivc_compress_exact")
+    return out
+
+
+def decompress_exact(fmt, w, out=None, stream=None):
+    """ivc_decompress_exact: every decoded component by the exact integer path."""
+    import torch
+    n = w.shape[0]
+    if out is None:
+        out = torch.empty(n, 3, dtype=torch.float32, device=w.device)
+    _chk(load().ivc_decompress_exact(ctypes.byref(fmt), _ptr(w), n, _ptr(out), _stream(stream)),
+         "ivc_decompress_exact")
     return out
 
 

@@ -86,3 +86,24 @@ def test_estimate_flag_band_covers_budget():
     budget = poly + rho + tail
     assert budget < 0.0045
     assert eps >= budget + 0.0005
+
+
+def test_bin_scale_constants():
+    """Each fast layout's bin scales N / (2 pi) (theta) and M / pi (phi) are
+    stored as float-float pairs: head = RN32 of the value, tail = RN32 of the
+    remainder."""
+    from mpmath import mp, mpf, pi
+    mp.prec = 200
+    src = open(SRC).read()
+    geos = {"GeoPrimary": (262143, 131071), "GeoSplit": (185363, 185362),
+            "GeoL1717": (131071, 131071), "GeoL1617": (131071, 65535)}
+    for g, (N, M) in geos.items():
+        body = src[src.index("struct %s {" % g):]
+        body = body[:body.index("};")]
+        vals = dict(re.findall(r"(C[TP][HL]) = (-?0x[0-9a-fA-Fp.+-]+)f", body))
+        assert set(vals) == {"CTH", "CTL", "CPH", "CPL"}, g
+        for (h, l), v in (((vals["CTH"], vals["CTL"]), mpf(N) / (2 * pi)),
+                          ((vals["CPH"], vals["CPL"]), mpf(M) / pi)):
+            hf, lf = float.fromhex(h), float.fromhex(l)
+            assert hf == float(np.float32(float(v))), (g, h)
+            assert lf == float(np.float32(float(v - mpf(hf)))), (g, l)
