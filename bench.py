@@ -427,6 +427,30 @@ def run_extras(args, fmt, a, b, wa, wb, stream, s_handle, n, pg, dev, value):
         del vc
     del va, vb
     torch.cuda.synchronize()
+    if n >= (1 << 26):
+        # the secondary workloads, short versions (each prints its own line with
+        # --workload at full size)
+        torch.cuda.empty_cache()
+        bt = batched_measure(5)
+        out["batched"] = {k: bt[k] for k in ("fields", "total_vectors", "tuned",
+                                              "graph_tuned_gvec_s", "status_tuned",
+                                              "separate_launches_gvec_s", "single_field_gvec_s",
+                                              "batched_over_single_field",
+                                              "graph_tuned_hbm_frac", "single_field_hbm_frac")}
+        torch.cuda.empty_cache()
+        tg = tgv_measure(48, 20, errors=False)
+        out["tgv_48"] = {k: tg[k] for k in ("n_vectors", "steps", "gvec_s", "gbs_36B",
+                                             "hbm_frac", "fp32_gvec_s")}
+        torch.cuda.empty_cache()
+        fd = fdiv_measure(48, 10, 3, 0, simt=False)
+        out["fdiv_48"] = {k: fd[k] for k in ("elements", "ms", "gbs_algorithmic", "hbm_frac",
+                                              "fp32_ms", "speedup_vs_fp32")}
+        out["fdiv_48"]["tensor_frac"] = fd["tensor"]["frac"]
+        torch.cuda.empty_cache()
+        fr = fr_measure(48, 10, 3, only=(7,))
+        out["fr_step7_48"] = fr["per_step"][0]
+        out["fr_step7_48"]["elements"] = fr["elements"]
+        torch.cuda.empty_cache()
     return out
 
 
@@ -586,16 +610,18 @@ def run_tgv(args):
     the 4^3 solution points of each hex of an E^3 mesh: v <- v + dt f with the
     pressure-gradient forcing, decompress -> update -> recompress, 100 steps;
     error against the FP64 trajectory, next to the same update on FP32x3."""
+    print(json.dumps(tgv_measure(args.tgv_elements, 100)), flush=True)
+
+
+def tgv_measure(E, nsteps, errors=True):
     import torch
 
     from paper_2003_02633_gb300 import ivc, synth
     dev = torch.device("cuda", 0)
     fmt = ivc.default_format()
-    E = args.tgv_elements
     v, f, rho = synth.tgv_fields_device(E, dev)
     n = v.shape[0]
     dt = 1e-3
-    nsteps = 100
     wv, wf = ivc.compress(fmt, v), ivc.compress(fmt, f)
     wm = torch.empty_like(wv)
     stream = torch.cuda.current_stream()
@@ -618,19 +644,31 @@ def run_tgv(args):
         d["max_abs_vs_fp64"] = float(diff.max())
         d["mean_abs_vs_fp64"] = float(diff.mean())
         return d
-    line = {"workload": "tgv_pointwise_update", "elements": E, "n_vectors": n, "steps": nsteps,
-            "dt": dt, "ms_per_step": round(ms / nsteps, 5), "gvec_s": _gvec(n, ms / nsteps),
+    hbm, _ = measured_peaks()
+    line = {"workload": "tgv_pointwise_update", "elements": E ** 3, "n_vectors": n,
+            "steps": nsteps, "dt": dt, "ms_per_step": round(ms / nsteps, 5),
+            "gvec_s": _gvec(n, ms / nsteps),
             "gbs_36B": round(36 * n / (ms / nsteps * 1e-3) / 1e9, 1),
+            "hbm_frac": round(36 * n / (ms / nsteps * 1e-3) / 1e9 / hbm, 4),
             "fp32_ms_per_step": round(ms32 / nsteps, 5), "fp32_gvec_s": _gvec(n, ms32 / nsteps),
-            "error_compressed_vs_fp64": err(vc), "error_fp32_vs_fp64": err(v32),
-            "note": "velocity w = 0 makes every initial vector a phi tie (z = 0)"}
-    print(json.dumps(line), flush=True)
+            "note": "velocity w = 0 makes every initial vector a phi tie (z = 0); 36 B per "
+                    "vector: v, f words and rho in, v and m words out"}
+    if errors:
+        line["error_compressed_vs_fp64"] = err(vc)
+        line["error_fp32_vs_fp64"] = err(v32)
+    return line
 
 
 def run_batched(args):
     """256 fields of uneven length (log-uniform 2^10..2^24), each with its own
     magnitude window: one persistent launch from a CUDA graph, against 256
     separate launches and one launch over a single field of the total size."""
+    print(json.dumps(batched_measure(max(5, min(args.steps, 50)), sweep=True)), flush=True)
+
+
+def batched_measure(steps, sweep=False):
+    """The batched workload; the plan's launch shape is the autotuner's
+    (ivc_tune_batched), plus, with sweep, fixed tiles for comparison."""
     import torch
 
     from paper_2003_02633_gb300 import ivc, synth
@@ -648,17 +686,25 @@ def run_batched(args):
     total = int(sum(int(m) for m in lens))
     stream = torch.cuda.current_stream()
     s = stream.cuda_stream
-    steps = max(5, min(args.steps, 50))
     out = {"workload": "batched_add", "fields": len(fields), "total_vectors": total}
-    for tile in (4096, 16384, 65536):
-        cfg = ivc.ivc_launch_config(256, 2, tile, 0)
-        plan = ivc.BatchedPlan(fmt, ivc.IVC_OP_ADD, fields, cfg=cfg, stream=s)
-        ms, _ = _time_ms(lambda: plan.launch(stream=s), steps, 3, stream)
-        out[f"graph_tile{tile}_gvec_s"] = _gvec(total, ms)
-        ms, _ = _time_ms(lambda: plan.launch(stream=s, graph=False), steps, 3, stream)
-        out[f"direct_tile{tile}_gvec_s"] = _gvec(total, ms)
-        out[f"status_tile{tile}"] = plan.status(stream=s)
-        plan.close()
+    best = ivc.tune_batched(fmt, ivc.IVC_OP_ADD, fields, stream=s)
+    out["tuned"] = {"block": best.block, "vec_per_thread": best.vec_per_thread,
+                    "tile": best.tile, "blocks_per_sm": best.blocks_per_sm}
+    plan = ivc.BatchedPlan(fmt, ivc.IVC_OP_ADD, fields, cfg=best, stream=s)
+    ms, _ = _time_ms(lambda: plan.launch(stream=s), steps, 3, stream)
+    out["graph_tuned_gvec_s"] = _gvec(total, ms)
+    out["status_tuned"] = plan.status(stream=s)
+    plan.close()
+    if sweep:
+        for tile in (4096, 16384, 65536):
+            cfg = ivc.ivc_launch_config(256, 2, tile, 0)
+            plan = ivc.BatchedPlan(fmt, ivc.IVC_OP_ADD, fields, cfg=cfg, stream=s)
+            ms, _ = _time_ms(lambda: plan.launch(stream=s), steps, 3, stream)
+            out[f"graph_tile{tile}_gvec_s"] = _gvec(total, ms)
+            ms, _ = _time_ms(lambda: plan.launch(stream=s, graph=False), steps, 3, stream)
+            out[f"direct_tile{tile}_gvec_s"] = _gvec(total, ms)
+            out[f"status_tile{tile}"] = plan.status(stream=s)
+            plan.close()
 
     def separate():
         for fa, fb, fc, _ in fields:
@@ -670,9 +716,13 @@ def run_batched(args):
     big_c = torch.empty_like(big_a)
     ms, _ = _time_ms(lambda: ivc.add(fmt, big_a, big_b, out=big_c, stream=s), steps, 3, stream)
     out["single_field_gvec_s"] = _gvec(total, ms)
-    best = max(v for k, v in out.items() if k.startswith("graph_tile"))
-    out["batched_over_single_field"] = round(best / out["single_field_gvec_s"], 4)
-    print(json.dumps(out), flush=True)
+    out["batched_over_single_field"] = round(out["graph_tuned_gvec_s"] /
+                                             out["single_field_gvec_s"], 4)
+    hbm, _ = measured_peaks()
+    out["graph_tuned_hbm_frac"] = round(out["graph_tuned_gvec_s"] * BYTES_PER_VEC / hbm, 4)
+    out["single_field_hbm_frac"] = round(out["single_field_gvec_s"] * BYTES_PER_VEC / hbm, 4)
+    del big_a, big_b, big_c, fields
+    return out
 
 
 def run_precision(args):
@@ -732,13 +782,17 @@ def run_fdiv(args):
     Euler flux of the TGV initial state on an E^3 hex mesh of degree 3 (64
     solution points, 5 flux rows per point), against the same operator on the
     uncompressed FP32 flux; FP32 arithmetic in both."""
+    print(json.dumps(fdiv_measure(args.fdiv_elements, args.steps, args.warmup,
+                                  args.cpu_seconds)), flush=True)
+
+
+def fdiv_measure(E, steps_arg, warmup_arg, cpu_seconds, simt=True):
     import numpy as np
     import torch
 
     from paper_2003_02633_gb300 import ivc, synth
     dev = torch.device("cuda", 0)
     fmt = ivc.default_format()
-    E = args.fdiv_elements
     order, nv = 3, 5
     ns = (order + 1) ** 3
     F = synth.tgv_euler_flux(E, order, device=dev)               # (ns, nv, ne, 3)
@@ -751,17 +805,20 @@ def run_fdiv(args):
     out32 = torch.empty_like(out)
     stream = torch.cuda.current_stream()
     s = stream.cuda_stream
-    steps, warmup = max(3, min(args.steps, 50)), max(3, min(args.warmup, 10))
+    steps, warmup = max(3, min(steps_arg, 50)), max(3, min(warmup_arg, 10))
     ms, per = time_launches(lambda: ivc.flux_divergence(fmt, W, D, out=out, stream=s), steps,
                             warmup, stream)
     ms32, per32 = time_launches(lambda: ivc.f32_flux_divergence(Fc, D, out=out32, stream=s),
                                 steps, warmup, stream)
     # the same two on the CUDA cores (FP32 FMAs)
     out_s = torch.empty_like(out)
-    ms_s, _ = time_launches(lambda: ivc.flux_divergence(fmt, W, D, out=out_s, stream=s,
-                                                        simt=True), steps, warmup, stream)
-    ms32_s, _ = time_launches(lambda: ivc.f32_flux_divergence(Fc, D, out=out_s, stream=s,
-                                                              simt=True), steps, warmup, stream)
+    ms_s = ms32_s = float("nan")
+    if simt:
+        ms_s, _ = time_launches(lambda: ivc.flux_divergence(fmt, W, D, out=out_s, stream=s,
+                                                            simt=True), steps, warmup, stream)
+        ms32_s, _ = time_launches(lambda: ivc.f32_flux_divergence(Fc, D, out=out_s, stream=s,
+                                                                  simt=True), steps, warmup,
+                                  stream)
     ivc.flux_divergence_check()
     t, t32 = ms / steps, ms32 / steps
     flop = 2.0 * 3 * ns * ns * nv                                   # per element
@@ -791,7 +848,10 @@ def run_fdiv(args):
             "max_abs_diff_vs_fp32_input": float(d.max()), "max_abs_fp32_result": float(scale),
             "bytes_per_element": {"compressed": bytes_c, "fp32": bytes_32},
             "data": "synthetic TGV initial state (Sec. 4.2), Euler flux rows, degree-3 hexes"}
-    if args.cpu_seconds > 0:
+    if not simt:
+        for k in ("simt_ms", "simt_fp32_ms", "tc_speedup_vs_simt", "tc_fp32_speedup_vs_simt"):
+            line.pop(k)
+    if cpu_seconds > 0:
         from oracle import oracle as O
         rng = np.random.default_rng(0)
         sel = np.sort(rng.choice(ne, size=min(ne, 256), replace=False))
@@ -804,7 +864,8 @@ def run_fdiv(args):
                                 "cores": 1, "kind": "oracle",
                                 "sample": f"{sel.size} random elements of the same mesh",
                                 "max_abs_diff_vs_gpu": float(np.abs(got - ref).max())}
-    print(json.dumps(line), flush=True)
+    del W, Fc, out, out32, out_s
+    return line
 
 
 def run_fr(args):
@@ -815,12 +876,17 @@ def run_fr(args):
     step timed on its own.  The bytes each step moves per element come from
     the memory model of Table mem_usage (fr_memory); its prediction is the
     byte ratio, the measurement the time ratio."""
+    print(json.dumps(fr_measure(args.fr_elements, args.steps, args.warmup)), flush=True)
+
+
+def fr_measure(E, steps_arg, warmup_arg, only=None):
+    """The FR steps; with `only`, just those steps are timed (the chain still
+    runs once in full so that every step has its inputs)."""
     import torch
 
     from paper_2003_02633_gb300 import fr_memory, ivc, synth
     dev = torch.device("cuda", 0)
     fmt = ivc.default_format()
-    E = args.fr_elements
     order = 3
     dims = (E, E, E)
     ne = E ** 3
@@ -879,12 +945,12 @@ def run_fr(args):
             r[st]()
     torch.cuda.synchronize()
     ivc.flux_divergence_check()
-    steps, warmup = max(3, min(args.steps, 20)), max(3, min(args.warmup, 5))
+    steps, warmup = max(3, min(steps_arg, 20)), max(3, min(warmup_arg, 5))
     hbm_gbs, _ = measured_peaks()
     rows = []
     tot = [0.0, 0.0]
     byt = [0, 0]
-    for st in order_steps:
+    for st in (only or order_steps):
         ms = [_time_ms(r[st], steps, warmup, stream)[0] for r in runs]
         b32 = fr_memory.step_bytes(order, st)
         bc = fr_memory.step_bytes(order, st, compressed=True)
@@ -895,7 +961,8 @@ def run_fr(args):
         rows.append({"step": st, "fp32_ms": round(ms[0], 4), "compressed_ms": round(ms[1], 4),
                      "time_ratio": round(ms[1] / ms[0], 4), "gamma_bytes": round(bc / b32, 4),
                      "fp32_gbs": round(b32 * ne / (ms[0] * 1e-3) / 1e9, 1),
-                     "compressed_gbs": round(bc * ne / (ms[1] * 1e-3) / 1e9, 1)})
+                     "compressed_gbs": round(bc * ne / (ms[1] * 1e-3) / 1e9, 1),
+                     "compressed_hbm_frac": round(bc * ne / (ms[1] * 1e-3) / 1e9 / hbm_gbs, 4)})
     ivc.flux_divergence_check()
     t_all, g_all = fr_memory.totals(order)
     line = {"workload": "fr_steps_5_11", "elements": ne, "order": order, "nvars": 5,
@@ -908,7 +975,7 @@ def run_fr(args):
             "hbm_peak_gbs": hbm_gbs,
             "data": "synthetic: Taylor-Green state (Sec. 4.2) with a 5% smooth perturbation "
                     "on a periodic hex mesh deformed by 0.1 sin-products, degree 3"}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_sweep(args):

@@ -249,6 +249,18 @@ ivc_status ivc_plan_destroy(ivc_plan plan);
 ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const uint64_t *b,
                     uint64_t *c, int64_t n, ivc_stream_t stream, ivc_launch_config *best);
 
+/* Autotuner of the batched form (no counterpart in the paper; results do
+ * not depend on the shape): builds plans for candidate shapes -- block size
+ * (128, 256), resident blocks per SM (1, 2, ... up to the occupancy limit)
+ * and work-list tile (2048 ... 131072 vectors) -- in the caller's workspace
+ * (ws_bytes as sized by ivc_plan_batched), times each with ordinary
+ * persistent launches on `stream` (the fields' outputs are overwritten) and
+ * writes the fastest to *best (vec_per_thread reports the kernel's vectors
+ * per thread per step: 2 on the packed fast path, else 1).  Synchronous. */
+ivc_status ivc_tune_batched(const ivc_format *fmt, ivc_op op, const ivc_field *fields,
+                            int nfields, void *workspace, size_t ws_bytes, ivc_stream_t stream,
+                            ivc_launch_config *best);
+
 /* Add with an explicit launch shape (cfg NULL = default). */
 ivc_status ivc_add_cfg(const ivc_format *fmt, const uint64_t *a, const uint64_t *b,
                        uint64_t *c, int64_t n, const ivc_launch_config *cfg,
@@ -304,6 +316,16 @@ ivc_status ivc_flux_divergence(const ivc_format *fmt, const uint64_t *F, int64_t
 ivc_status ivc_flux_divergence_simt(const ivc_format *fmt, const uint64_t *F, int64_t ld, int ns,
                                     int nvars, int64_t ne, const float *D, float *div,
                                     int64_t ld_out, ivc_stream_t stream);
+
+/* Bound, in SM clock cycles, of every wait between the decoding and the
+ * accumulating warps of the CUDA-core kernel (ivc_flux_divergence_simt,
+ * ivc_f32_flux_divergence_simt) launched after this call; cycles <= 0
+ * restores the default (2e9, about a second).  A wait that runs out ends the
+ * block (its copies completed first) and makes the next
+ * ivc_flux_divergence_check return IVC_ERR_TIMEOUT; the output of that launch
+ * is undefined.  Meant for testing that failure path; host state, not
+ * thread-safe against concurrent launches. */
+ivc_status ivc_set_flux_divergence_wait_limit(long long cycles);
 
 /* Reports (and clears) a failure of the flux-divergence kernels since the
  * last check: their decoding and accumulating warps hand shared-memory

@@ -587,6 +587,11 @@ ivc_status ivc_flux_divergence_simt(const ivc_format *fmt, const uint64_t *F, in
   return flux_divergence(false, fmt, F, ld, ns, nvars, ne, D, div, ld_out, stream);
 }
 
+ivc_status ivc_set_flux_divergence_wait_limit(long long cycles) {
+  set_flux_div_wait_limit(cycles);
+  return IVC_OK;
+}
+
 ivc_status ivc_flux_divergence_check(void) {
   int status = 0, status_tc = 0;
   if (flux_div_status(&status) != cudaSuccess || flux_div_tc_status(&status_tc) != cudaSuccess) {
@@ -956,6 +961,68 @@ ivc_status ivc_plan_destroy(ivc_plan plan) {
 }
 
 // ------------------------------------------------------------------ tuner
+
+ivc_status ivc_tune_batched(const ivc_format *fmt, ivc_op op, const ivc_field *fields,
+                            int nfields, void *workspace, size_t ws_bytes, ivc_stream_t stream,
+                            ivc_launch_config *best) {
+  if (!best || !fields || nfields < 1 || !workspace) return IVC_ERR_ARG;
+  DevFormat F;
+  int map;
+  ivc_status st = make_devformat(fmt, &F, &map);
+  if (st != IVC_OK) return st;
+  const bool fastp = fast::fast_geometry(map, F) != 0;
+  const int kind = op == IVC_OP_ADD ? (fastp ? K_BATCH_ADD_FAST : K_BATCH_ADD)
+                                    : (fastp ? K_BATCH_AXPY_FAST : K_BATCH_AXPY);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return IVC_ERR_CUDA;
+  }
+  const int blocks[] = {128, 256};
+  const int tiles[] = {2048, 8192, 32768, 131072};
+  float best_ms = 1e30f;
+  ivc_launch_config bc{256, fastp ? 2 : 1, 8192, 0};
+  ivc_status err = IVC_OK;
+  for (int blk : blocks) {
+    const int occ = occupancy(map, kind, blk, kernel_smem_bytes(F, map, kind, blk));
+    for (int bps = 1; bps <= occ && err == IVC_OK; bps = (bps * 2 > occ && bps < occ) ? occ : bps * 2) {
+      for (int tile : tiles) {
+        const ivc_launch_config cfg{blk, fastp ? 2 : 1, tile, bps};
+        size_t ws = ws_bytes;
+        ivc_plan plan = nullptr;
+        err = ivc_plan_batched(fmt, op, fields, nfields, workspace, &ws, &cfg, stream, &plan);
+        if (err != IVC_OK) break;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && err == IVC_OK; ++rep) {
+          cudaEventRecord(e0, stream);
+          err = ivc_launch_plan_direct(plan, stream);
+          cudaEventRecord(e1, stream);
+          if (err == IVC_OK && cudaEventSynchronize(e1) != cudaSuccess) err = IVC_ERR_CUDA;
+          float ms = 0.0f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0 && ms < ms_min) ms_min = ms;
+        }
+        const ivc_status ps = err == IVC_OK ? ivc_plan_status(plan, stream) : err;
+        ivc_plan_destroy(plan);
+        if (err == IVC_OK) err = ps;
+        if (err != IVC_OK) break;
+        if (ms_min < best_ms) {
+          best_ms = ms_min;
+          bc = cfg;
+        }
+      }
+    }
+    if (err != IVC_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != IVC_OK) {
+    cudaGetLastError();
+    return err;
+  }
+  *best = bc;
+  return IVC_OK;
+}
 
 ivc_status ivc_tune(const ivc_format *fmt, ivc_op op, const uint64_t *a, const uint64_t *b,
                     uint64_t *c, int64_t n, ivc_stream_t stream, ivc_launch_config *best) {

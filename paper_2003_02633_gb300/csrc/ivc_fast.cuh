@@ -363,8 +363,8 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 
 // beta = atan(mn / mx) in [0, pi/4] for 0 <= mn <= mx, as an unevaluated sum
 // bh + bl with |error| < 5e-8 rad:
-//   * q = mn / mx as a float-float qh + ql (Newton-refined reciprocal and the
-//     exact residual mn - mx qh);
+//   * q = mn / mx as a float-float qh + ql (approximate reciprocal, then the
+//     exact residual mn - mx qh times it: the quotient's own error cancels);
 //   * atan(q) = q + q^3 R(q^2), R a degree-7 polynomial from a
 //     least-squares-minimax (Lawson) fit on [0, 1] (7.4e-9 in exact
 //     arithmetic), kept as q + s so that FP32 rounding acts on s only;
@@ -373,8 +373,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // mx = 0 (zero vector in this plane) gives beta = 0.
 __device__ __forceinline__ void atan_ratio2(float2 mn, float2 mx, float2 &bh, float2 &bl) {
   const float2 m = make_float2(fmaxf(mx.x, 1e-30f), fmaxf(mx.y, 1e-30f));
-  float2 r = make_float2(rcp_approx(m.x), rcp_approx(m.y));
-  r = fma2(r, fma2(neg2(m), r, bc(1.0f)), r);
+  const float2 r = make_float2(rcp_approx(m.x), rcp_approx(m.y));
   const float2 qh = mul2(mn, r);
   const float2 ql = mul2(fma2(neg2(m), qh, mn), r);
   const float2 q2 = mul2(qh, qh);
@@ -393,9 +392,10 @@ __device__ __forceinline__ void atan_ratio2(float2 mn, float2 mx, float2 &bh, fl
 
 // Bin coordinate t = K0 + s1 * C * beta (K0 a multiple of 1/4, s1 = +-1,
 // C = n_max / pi or n_max / (2 pi) in float-float), returned as floor and
-// fraction computed without rounding the large sum: C beta = G + small
-// (exact products and TwoSum), G = Gi + Gf with Gi integral, then
-// t = [K0 + s1 Gi] + s1 (Gf + small).  Error below 0.002 bin.
+// fraction computed without rounding the large sum: C beta = G + small with
+// G = RN(Ch bh) and small = its exact rounding error (an FMA) plus the tail
+// products, G = Gi + Gf with Gi integral, then t = [K0 + s1 Gi] + s1 (Gf +
+// small).  Error below 0.002 bin.
 struct BinCoord2 {
   float2 fl, fr;  // floor(t) (exact integer-valued floats) and t - floor(t)
 };
@@ -406,13 +406,9 @@ __device__ __forceinline__ float2 floor2(float2 v) {  // |v| < 2^22
 
 __device__ __forceinline__ BinCoord2 bin_coord2(float2 K0, float2 s1, float2 bh, float2 bl, float Ch,
                                                 float Cl) {
-  const float2 p1 = mul2(bc(Ch), bh);
-  const float2 e1 = fma2(bc(Ch), bh, neg2(p1));
-  const float2 p2 = mul2(bc(Ch), bl);
-  const float2 G = add2(p1, p2);                          // TwoSum(p1, p2)
-  const float2 bv = sub2(G, p1);
-  const float2 E2 = add2(sub2(p1, sub2(G, bv)), sub2(p2, bv));
-  const float2 small = fma2(bc(Cl), bh, add2(E2, e1));
+  const float2 G = mul2(bc(Ch), bh);                       // C beta, head
+  // the head's exact rounding error and the tail products
+  const float2 small = fma2(bc(Ch), bl, fma2(bc(Cl), bh, fma2(bc(Ch), bh, neg2(G))));
   const float2 Gi = floor2(G);
   const float2 gfrac = add2(sub2(G, Gi), small);          // in (-0.01, 1.01)
   const float2 hI = fma2(s1, Gi, K0);                     // exact, quarter-integral

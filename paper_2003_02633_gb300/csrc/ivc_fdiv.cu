@@ -36,7 +36,9 @@ constexpr int kConsumers = 256; // 8 warps
 constexpr int kThreads = kProducers + kConsumers;
 constexpr int kXBuf = kJC * kMaxNv * 3 * kTE;   // floats per decoded buffer
 constexpr int kWBuf = kJC * kMaxNv * kTE * 3;   // 32-bit units per raw buffer (FP32 rows)
-constexpr long long kWaitCycles = 2000000000ll; // about a second
+constexpr long long kWaitCycles = 2000000000ll; // default bound of each wait: about a second
+// the bound every launch gets (ivc_set_flux_divergence_wait_limit)
+long long g_wait_cycles = kWaitCycles;
 // the consumers cover 64 points (16 groups of 4) x the tile's elements (groups of 4)
 static_assert(kConsumers == 16 * (kTE / 4), "consumer mapping");
 static_assert(kProducers % (kTE / 2) == 0, "producer mapping");
@@ -79,9 +81,13 @@ __device__ __forceinline__ void cp_async_wait_1() {
   asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Waits for the completion of the barrier phase with the given parity;
-// false when about a second of cycles passed first.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// false when `limit` cycles (about a second by default) passed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
   const uint32_t a = smem_addr(bar);
   const long long t0 = clock64();
   while (true) {
@@ -93,7 +99,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -162,7 +168,7 @@ template <int MODE, int MAP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_flux_div(const __grid_constant__ DevFormat F, const void *__restrict__ src, int64_t ld,
                int ns, int nv, int64_t ne, const float *__restrict__ D, float *__restrict__ div,
-               int64_t ld_out) {
+               int64_t ld_out, long long wait_limit) {
   extern __shared__ __align__(16) unsigned char fd_smem[];
   TabEntry *tabs = reinterpret_cast<TabEntry *>(fd_smem);
   const int ntab = (MODE == FD_F32 || MAP == MAP_TANH) ? 0 : F.nent_t + F.nent_p;
@@ -216,12 +222,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       cp_async_wait_1();
       const int b = g & 1;
       const uint32_t u = g >> 1;
-      if (u >= 1 && !mbar_wait(bars + 2 + b, (u - 1) & 1u)) {
+      if (u >= 1 && !mbar_wait(bars + 2 + b, (u - 1) & 1u, wait_limit)) {
         *abort_flag = 1;
         atomicExch(&g_fdiv_status, 1);
+        cp_async_wait_all();  // no copy of this thread outlives it
         return;
       }
-      if (*abort_flag) return;
+      if (*abort_flag) {
+        cp_async_wait_all();
+        return;
+      }
       const int jn = min(kJC, ns - ch * kJC);
       float *X = Xs + b * kXBuf;
       const uint32_t *Wb = Ws + b * kWBuf;
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int ch = 0; ch < nchunk; ++ch, ++g) {
       const int b = g & 1;
       const uint32_t u = g >> 1;
-      if (!mbar_wait(bars + b, u & 1u)) {
+      if (!mbar_wait(bars + b, u & 1u, wait_limit)) {
         *abort_flag = 1;
         atomicExch(&g_fdiv_status, 1);
         return;
@@ -368,7 +378,7 @@ cudaError_t launch_one(const DevFormat &F, const void *src, int64_t ld, int ns, 
   int64_t grid = (int64_t)sms * occ;
   if (grid > ntiles) grid = ntiles;
   k_flux_div<MODE, MAP><<<(int)grid, kThreads, smem, st>>>(F, src, ld, ns, nv, ne, D, div,
-                                                            ld_out);
+                                                            ld_out, g_wait_cycles);
   return cudaGetLastError();
 }
 
@@ -389,6 +399,10 @@ cudaError_t launch_flux_div(int map, bool fast_path, bool f32, const DevFormat &
     default:
       return launch_one<FD_GENERIC, MAP_FRACSPLIT>(F, src, ld, ns, nv, ne, D, div, ld_out, st);
   }
+}
+
+void set_flux_div_wait_limit(long long cycles) {
+  g_wait_cycles = cycles > 0 ? cycles : kWaitCycles;
 }
 
 cudaError_t flux_div_status(int *status) {

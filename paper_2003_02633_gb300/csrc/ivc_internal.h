@@ -141,6 +141,9 @@ cudaError_t flux_div_tc_status(int *status);
 // Reads and clears the flux-divergence kernels' device status word (1: a
 // bounded wait between the decoding and the accumulating warps ran out).
 cudaError_t flux_div_status(int *status);
+// Bound (clock cycles) of every wait of the CUDA-core flux-divergence kernel
+// launched from now on; <= 0 restores the default (about a second).
+void set_flux_div_wait_limit(long long cycles);
 
 // Resident blocks per SM of a kernel at a block size (0 if it cannot run).
 int occupancy(int map, int kind, int block, size_t smem);

@@ -440,6 +440,12 @@ __global__ void __launch_bounds__(256) k_batched(const __grid_constant__ DevForm
     }
     const FieldDesc fd = P.fields[lo];
     const int64_t start = (tile - P.tile_start[lo]) * (int64_t)P.tile;
+    // a work-list entry that names no range inside its field (a plan whose
+    // workspace was overwritten) is skipped and reported
+    if (start < 0 || start >= fd.n) {
+      if (threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_ARG);
+      continue;
+    }
     const int64_t len = min((int64_t)P.tile, fd.n - start);
     const uint64_t *a = fd.a + start;
     const uint64_t *b = (OP == IVC_OP_ADD ? fd.b : fd.c) + start;
@@ -481,6 +487,12 @@ __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ De
     }
     const FieldDesc fd = P.fields[lo];
     const int64_t start = (tile - P.tile_start[lo]) * (int64_t)P.tile;
+    // a work-list entry that names no range inside its field (a plan whose
+    // workspace was overwritten) is skipped and reported
+    if (start < 0 || start >= fd.n) {
+      if (threadIdx.x == 0) atomicExch(P.status, (int)IVC_ERR_ARG);
+      continue;
+    }
     const int64_t len = min((int64_t)P.tile, fd.n - start);
     const uint64_t *a = fd.a + start;
     const uint64_t *b = (OP == IVC_OP_ADD ? fd.b : fd.c) + start;

@@ -97,7 +97,10 @@ _SIGS = {
     "ivc_launch_plan_direct": [_P, _P],
     "ivc_plan_status": [_P, _P],
     "ivc_plan_destroy": [_P],
+    "ivc_set_flux_divergence_wait_limit": [ctypes.c_longlong],
     "ivc_tune": [_FMT, _I, _P, _P, _P, _I64, _P, ctypes.POINTER(ivc_launch_config)],
+    "ivc_tune_batched": [_FMT, _I, _P, _I, _P, ctypes.c_size_t, _P,
+                         ctypes.POINTER(ivc_launch_config)],
     "ivc_add_noalloc": [_FMT, _P, _P, _P, _I64, _P],
     "ivc_flux_divergence": [_FMT, _P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
     "ivc_flux_divergence_simt": [_FMT, _P, _I64, _I, _I, _I64, _P, _P, _I64, _P],
@@ -583,6 +586,25 @@ class BatchedPlan:
             self.close()
         except Exception:
             pass
+
+
+def tune_batched(fmt, op, fields, stream=None) -> ivc_launch_config:
+    """ivc_tune_batched over a list of (a, b, c, alpha) tensor fields."""
+    import torch
+    L = load()
+    arr = (ivc_field * len(fields))()
+    for i, (a, b, c, alpha) in enumerate(fields):
+        arr[i] = ivc_field(_ptr(a), _ptr(b) if b is not None else None, _ptr(c), a.shape[0],
+                           float(alpha), 0.0)
+    ws = ctypes.c_size_t(0)
+    _chk(L.ivc_plan_batched(ctypes.byref(fmt), op, arr, len(fields), None, ctypes.byref(ws),
+                            None, _stream(stream), None), "ivc_plan_batched(size)")
+    buf = torch.empty(ws.value + 256, dtype=torch.uint8, device=fields[0][0].device)
+    base = (buf.data_ptr() + 255) // 256 * 256
+    best = ivc_launch_config()
+    _chk(L.ivc_tune_batched(ctypes.byref(fmt), op, arr, len(fields), base, ws.value,
+                            _stream(stream), ctypes.byref(best)), "ivc_tune_batched")
+    return best
 
 
 def tune(fmt, op, a, b, c, stream=None) -> ivc_launch_config:

@@ -164,3 +164,48 @@ def test_fr_argument_errors_before_device_work(lib):
     assert fc(ref(bad), ref(B), a8, a8, 4, 4, 5, a8, None) == ivc.IVC_ERR_FORMAT
     assert fc(ref(f), ref(B), a8, a8, 4, 3, 5, a8, None) == ivc.IVC_ERR_ARG
     assert lib.ivc_f32_fr_flux_correction(ref(B), a8, a8, 4, 4, 0, a8, None) == ivc.IVC_ERR_ARG
+
+
+def test_plan_workspace_too_small(lib):
+    """ivc_plan_batched reports a workspace smaller than it needs before it
+    touches the workspace or the device."""
+    f = ivc.default_format()
+    arr = (ivc.ivc_field * 3)()
+    ws = ctypes.c_size_t(0)
+    assert lib.ivc_plan_batched(ctypes.byref(f), ivc.IVC_OP_ADD, arr, 3, None, ctypes.byref(ws),
+                                None, None, None) == ivc.IVC_OK
+    assert ws.value > 0
+    small = ctypes.c_size_t(ws.value - 8)
+    plan = ctypes.c_void_p()
+    fake = 4096          # never dereferenced: the size check comes first
+    assert lib.ivc_plan_batched(ctypes.byref(f), ivc.IVC_OP_ADD, arr, 3, fake,
+                                ctypes.byref(small), None, None,
+                                ctypes.byref(plan)) == ivc.IVC_ERR_NOMEM
+    assert not plan.value
+
+
+@pytest.mark.parametrize("entry", ["add", "axpy", "compress", "decompress", "add_noalloc",
+                                   "compress_exact", "plan_batched"])
+def test_invalid_format_rejected_by_entry_points(lib, entry):
+    """A format that fails validation is rejected by every entry point before
+    any device work (IVC_ERR_FORMAT), whatever the pointers."""
+    bad = ivc.make_format(exp_bits=9)
+    B = ctypes.byref(bad)
+    p = 4096
+    calls = {
+        "add": lambda: lib.ivc_add(B, p, p, p, 16, None),
+        "axpy": lambda: lib.ivc_axpy(B, 0.5, p, p, 16, None),
+        "compress": lambda: lib.ivc_compress(B, p, 0, 0, 16, p, None, None),
+        "decompress": lambda: lib.ivc_decompress(B, p, 16, p, 0, 0, None),
+        "add_noalloc": lambda: lib.ivc_add_noalloc(B, p, p, p, 16, None),
+        "compress_exact": lambda: lib.ivc_compress_exact(B, p, 16, p, None, None),
+    }
+    if entry == "plan_batched":
+        arr = (ivc.ivc_field * 1)()
+        ws = ctypes.c_size_t(1 << 20)
+        plan = ctypes.c_void_p()
+        st = lib.ivc_plan_batched(B, ivc.IVC_OP_ADD, arr, 1, p, ctypes.byref(ws), None, None,
+                                  ctypes.byref(plan))
+    else:
+        st = calls[entry]()
+    assert st == ivc.IVC_ERR_FORMAT

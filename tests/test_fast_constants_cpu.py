@@ -30,11 +30,13 @@ def _fma(a, b, c):
 
 
 def _atan_ratio(mn, mx):
-    """The kernel's steps: Newton-refined reciprocal, double-float quotient,
+    """The kernel's steps: approximate reciprocal, float-float quotient,
     q + q^3 R(q^2) with the ql term at slope 1 - q^2/2."""
     m = np.maximum(mx, F32(1e-30))
+    # rcp.approx: within an ulp of 1/m; perturbed by up to one ulp either way
     r = (F32(1.0) / m).astype(F32)
-    r = _fma(r, _fma(-m, r, np.ones_like(m)), r)
+    r = np.where(np.arange(r.size) % 3 == 0, np.nextafter(r, F32(np.inf)),
+                 np.where(np.arange(r.size) % 3 == 1, np.nextafter(r, F32(0)), r)).astype(F32)
     qh = (mn * r).astype(F32)
     ql = (_fma(-m, qh, mn) * r).astype(F32)
     q2 = (qh * qh).astype(F32)
