@@ -47,7 +47,7 @@ def parse_args():
     p.add_argument("--no-extra", action="store_true", help="skip the baseline/extra measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--workload", choices=["add", "tgv", "batched", "precision", "fdiv", "sweep",
-                                          "gather", "fr"],
+                                          "gather", "fr", "codec"],
                    default="add",
                    help="add: the headline line; the others print their own JSON line")
     p.add_argument("--tgv-elements", type=int, default=96)
@@ -1066,6 +1066,45 @@ def run_gather(args):
     print(json.dumps(line), flush=True)
 
 
+def run_codec(args):
+    """The fast codec's kernels once each, in a fixed order, at N = 2^log2n
+    (the target of the per-kernel ncu captures under profiles/): compress a,
+    compress b (k_compress_fast), add (k_fused_fast<0>), axpy in place on b's
+    words (k_fused_fast<1>), decompress of the sum (k_decompress_fast), each
+    launch timed with CUDA events after `warmup` untimed rounds of the same
+    sequence."""
+    import torch
+
+    from paper_2003_02633_gb300 import ivc, synth
+    dev = torch.device("cuda", 0)
+    fmt = ivc.default_format()
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    n = 1 << args.log2n
+    a = synth.device_vectors(n, 41, dev)
+    b = synth.device_vectors(n, 42, dev)
+    wa, wb, wc = (torch.empty(n, dtype=torch.int64, device=dev) for _ in range(3))
+    d = torch.empty_like(a)
+    seq = (("compress_a", lambda: ivc.compress(fmt, a, out=wa, stream=s)),
+           ("compress_b", lambda: ivc.compress(fmt, b, out=wb, stream=s)),
+           ("add", lambda: ivc.add(fmt, wa, wb, out=wc, stream=s)),
+           ("axpy", lambda: ivc.axpy(fmt, 0.7, wa, wb, stream=s)),
+           ("decompress", lambda: ivc.decompress(fmt, wc, out=d, stream=s)))
+    for _ in range(args.warmup):
+        for _, fn in seq:
+            fn()
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in seq:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = {"ms": round(e0.elapsed_time(e1), 4), "gvec_s": _gvec(n, e0.elapsed_time(e1))}
+    print(json.dumps({"workload": "codec_kernels", "n": n, "results": res}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -1080,6 +1119,8 @@ def main():
         run_fdiv(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "codec":
+        run_codec(args)
     elif args.workload == "gather":
         run_gather(args)
     elif args.workload == "fr":

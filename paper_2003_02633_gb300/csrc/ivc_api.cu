@@ -126,9 +126,24 @@ struct TableKey {
 
 struct TableSet {
   TabEntry *dev = nullptr;
-  size_t n_uniform_t = 0, n_uniform_p = 0;
+  size_t n_uniform_t = 0, n_uniform_p = 0, off_phi = 0;
   size_t off_dec_t = 0, off_dec_p = 0, off_bnd_t = 0, off_bnd_p = 0;
 };
+
+// cos, sin of pi k / M for k = 0 .. floor(M / 2): the per-code phi^ table of
+// the fast decoders (exact values at k = 0 and 2k = M).
+void phi_code_table(int M, std::vector<TabEntry> &out) {
+  for (int k = 0; 2 * k <= M; ++k) {
+    if (k == 0) {
+      out.push_back(TabEntry{1.0f, 0.0f, 0.0f, 0.0f});
+    } else if (2 * k == M) {
+      out.push_back(TabEntry{0.0f, 0.0f, 1.0f, 0.0f});
+    } else {
+      const long double a = kPiL * (long double)k / (long double)M;
+      out.push_back(entry_of(cosl(a), sinl(a)));
+    }
+  }
+}
 
 std::mutex g_mu;
 std::map<TableKey, TableSet> g_tables;
@@ -174,6 +189,8 @@ ivc_status get_tables(const ivc_format *f, const Geometry &g, int device, TableS
     ts.n_uniform_t = host.size();
     uniform_table(2 * g.M, host);
     ts.n_uniform_p = host.size() - ts.n_uniform_t;
+    ts.off_phi = host.size();
+    phi_code_table(g.M, host);
   }
   void *d = nullptr;
   if (cudaMalloc(&d, host.size() * sizeof(TabEntry)) != cudaSuccess) {
@@ -269,6 +286,7 @@ ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
   st = get_tables(f, g, dev, &ts);
   if (st != IVC_OK) return st;
   F->tab = ts.dev;
+  if (f->map != IVC_MAP_TANH) F->phi_tab = ts.dev + ts.off_phi;
   if (f->map == IVC_MAP_TANH) {
     F->dec_t = ts.dev + ts.off_dec_t;
     F->dec_p = ts.dev + ts.off_dec_p;

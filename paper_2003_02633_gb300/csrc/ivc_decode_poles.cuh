@@ -44,7 +44,7 @@ __device__ __forceinline__ void decode2_poles(uint64_t w0, uint64_t w1, const De
                                               const TabEntry *tab_t, const TabEntry *tab_p,
                                               float2 &X, float2 &Y, float2 &Z) {
   bool s0, s1;
-  decode2<G>(w0, w1, tab_t, tab_p, F.Kt_h, F.Kt_l, F.Kp_h, F.Kp_l, X, Y, Z, s0, s1);
+  decode2<G, true>(w0, w1, F, tab_t, tab_p, X, Y, Z, s0, s1);
   if (s0) pole_or_generic<G>(w0, F, tab_t, tab_p, X.x, Y.x, Z.x);
   if (s1) pole_or_generic<G>(w1, F, tab_t, tab_p, X.y, Y.y, Z.y);
 }
@@ -76,9 +76,9 @@ __device__ __forceinline__ void decode2_near(uint64_t w0, uint64_t w1, const Dev
   const float2 ntf = add2(make_float2(__uint_as_float(nt0 | 0x4B000000u),
                                       __uint_as_float(nt1 | 0x4B000000u)),
                           bc(-8388608.0f));
-  const float2 npf = add2(make_float2(__uint_as_float(np0 | 0x4B000000u),
-                                      __uint_as_float(np1 | 0x4B000000u)),
-                          bc(-8388608.0f));
+  FF2 cp, sp;
+  bool pneg0, pneg1;
+  phi_pair<G, true>(np0, np1, F, tab_p, cp, sp, pneg0, pneg1);
   const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)G::N));
   const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)G::N);
   FF2 cc, ss;
@@ -88,13 +88,6 @@ __device__ __forceinline__ void decode2_near(uint64_t w0, uint64_t w1, const Dev
   ct.l = sel2(ft.swap0, ft.swap1, ss.l, cc.l);
   st.h = sel2(ft.swap0, ft.swap1, cc.h, ss.h);
   st.l = sel2(ft.swap0, ft.swap1, cc.l, ss.l);
-  const Fold2 fp = fold2(add2(npf, npf), (float)(2 * G::M));
-  sincos2<G::SP>(fp.b, tab_p, F.Kp_h, F.Kp_l, cc, ss);
-  FF2 cp, sp;
-  cp.h = sel2(fp.swap0, fp.swap1, ss.h, cc.h);
-  cp.l = sel2(fp.swap0, fp.swap1, ss.l, cc.l);
-  sp.h = sel2(fp.swap0, fp.swap1, cc.h, ss.h);
-  sp.l = sel2(fp.swap0, fp.swap1, cc.l, ss.l);
   const float2 r = make_float2(r0, r1);
   FF2 R;
   prod2(r, sp, R.h, R.l);
@@ -107,7 +100,7 @@ __device__ __forceinline__ void decode2_near(uint64_t w0, uint64_t w1, const Dev
   const float2 z = add2(P, T);
   X = fma2(x, make_float2(ft.cneg0 ? -1.0f : 1.0f, ft.cneg1 ? -1.0f : 1.0f), bc(0.0f));
   Y = fma2(y, make_float2(copysignf(1.0f, mt.x), copysignf(1.0f, mt.y)), bc(0.0f));
-  Z = fma2(z, make_float2(fp.cneg0 ? -1.0f : 1.0f, fp.cneg1 ? -1.0f : 1.0f), bc(0.0f));
+  Z = fma2(z, make_float2(pneg0 ? -1.0f : 1.0f, pneg1 ? -1.0f : 1.0f), bc(0.0f));
   if (E0 == G::EALL) {
     const float3 v = decode_generic<G::MAP>(w0, F, tab_t, tab_p);
     X.x = v.x; Y.x = v.y; Z.x = v.z;

@@ -80,6 +80,10 @@ struct DevFormat {
   uint64_t Kxt_m, Kxp_m;            // pi / (2 D) = Kx_m 2^Kx_e (64-bit, exact paths)
   int32_t Kxt_e, Kxp_e;
   const TabEntry *tab;              // global, nent_t + nent_p entries
+  // uniform / fractional split: cos, sin of phi^_k = pi k / M for k = 0 ..
+  // floor(M / 2), one entry per code of the lower half of the phi range
+  // (global; read by the fast decoders; null where a caller has no table)
+  const TabEntry *phi_tab;
   uint64_t div_magic;               // ceil(2^64 / (N + 1)) for the split
   // tanh companding
   float gam, tanh_c, tanh_inv2c;    // gamma, c = tanh(gamma), 1 / (2c)

@@ -283,12 +283,49 @@ __device__ __forceinline__ void prod3(FF2 R, FF2 a, float2 &P, float2 &T) {
 
 __device__ __forceinline__ float apply_neg(float v, bool n) { return (n && v != 0.0f) ? -v : v; }
 
+// cos and sin (float-float magnitudes) of phi^ = pi n / M for both elements,
+// and whether cos phi^ is negative.  PT: one 16-byte load per element from
+// the per-code table of k = min(n, M - n) (cos(pi - a) = -cos a, sin(pi -
+// a) = sin a), read through L2; otherwise the angle is folded onto [0, pi/4]
+// and evaluated from the shared-memory head table and a Taylor step.
+template <class G, bool PT>
+__device__ __forceinline__ void phi_pair(uint32_t np0, uint32_t np1, const DevFormat &F,
+                                         const TabEntry *__restrict__ tab_p, FF2 &cp, FF2 &sp,
+                                         bool &cneg0, bool &cneg1) {
+  if (PT) {
+    const int m0 = G::M - (int)np0, m1 = G::M - (int)np1;
+    cneg0 = (int)np0 > m0;
+    cneg1 = (int)np1 > m1;
+    const float4 *t = reinterpret_cast<const float4 *>(F.phi_tab);
+    const float4 e0 = __ldg(t + min((int)np0, m0));
+    const float4 e1 = __ldg(t + min((int)np1, m1));
+    cp.h = make_float2(e0.x, e1.x);
+    cp.l = make_float2(e0.y, e1.y);
+    sp.h = make_float2(e0.z, e1.z);
+    sp.l = make_float2(e0.w, e1.w);
+  } else {
+    const float2 npf = add2(make_float2(__uint_as_float(np0 | 0x4B000000u),
+                                        __uint_as_float(np1 | 0x4B000000u)),
+                            bc(-8388608.0f));
+    // phi^ = pi (2 n_phi) / (2M)
+    const Fold2 fp = fold2(add2(npf, npf), (float)(2 * G::M));
+    FF2 cc, ss;
+    sincos2<G::SP>(fp.b, tab_p, F.Kp_h, F.Kp_l, cc, ss);
+    cp.h = sel2(fp.swap0, fp.swap1, ss.h, cc.h);
+    cp.l = sel2(fp.swap0, fp.swap1, ss.l, cc.l);
+    sp.h = sel2(fp.swap0, fp.swap1, cc.h, ss.h);
+    sp.l = sel2(fp.swap0, fp.swap1, cc.l, ss.l);
+    cneg0 = fp.cneg0;
+    cneg1 = fp.cneg1;
+  }
+}
+
 // Decodes two words; returns false in *ok for an element that needs the
 // generic path (non-finite word or an ambiguous rounding).
-template <class G>
-__device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry *__restrict__ tab_t,
-                                        const TabEntry *__restrict__ tab_p, float Kt_h,
-                                        float Kt_l, float Kp_h, float Kp_l, float2 &X,
+template <class G, bool PT>
+__device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const DevFormat &F,
+                                        const TabEntry *__restrict__ tab_t,
+                                        const TabEntry *__restrict__ tab_p, float2 &X,
                                         float2 &Y, float2 &Z, bool &slow0, bool &slow1) {
   const uint32_t hi0 = (uint32_t)(w0 >> 32), lo0 = (uint32_t)w0;
   const uint32_t hi1 = (uint32_t)(w1 >> 32), lo1 = (uint32_t)w1;
@@ -302,30 +339,24 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry
   uint32_t nt0, np0, nt1, np1;
   G::unpack(hi0, lo0, nt0, np0);
   G::unpack(hi1, lo1, nt1, np1);
+  // phi^ first: with the per-code table its loads are in flight while theta^
+  // is evaluated
+  FF2 cp, sp;
+  bool pneg0, pneg1;
+  phi_pair<G, PT>(np0, np1, F, tab_p, cp, sp, pneg0, pneg1);
   const float2 ntf = add2(make_float2(__uint_as_float(nt0 | 0x4B000000u),
                                       __uint_as_float(nt1 | 0x4B000000u)),
-                          bc(-8388608.0f));
-  const float2 npf = add2(make_float2(__uint_as_float(np0 | 0x4B000000u),
-                                      __uint_as_float(np1 | 0x4B000000u)),
                           bc(-8388608.0f));
   // theta^ = pi (2 n_theta - N) / N
   const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)G::N));
   const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)G::N);
   FF2 cc, ss;
-  sincos2<G::ST>(ft.b, tab_t, Kt_h, Kt_l, cc, ss);
+  sincos2<G::ST>(ft.b, tab_t, F.Kt_h, F.Kt_l, cc, ss);
   FF2 ct, st;
   ct.h = sel2(ft.swap0, ft.swap1, ss.h, cc.h);
   ct.l = sel2(ft.swap0, ft.swap1, ss.l, cc.l);
   st.h = sel2(ft.swap0, ft.swap1, cc.h, ss.h);
   st.l = sel2(ft.swap0, ft.swap1, cc.l, ss.l);
-  // phi^ = pi (2 n_phi) / (2M)
-  const Fold2 fp = fold2(add2(npf, npf), (float)(2 * G::M));
-  sincos2<G::SP>(fp.b, tab_p, Kp_h, Kp_l, cc, ss);
-  FF2 cp, sp;
-  cp.h = sel2(fp.swap0, fp.swap1, ss.h, cc.h);
-  cp.l = sel2(fp.swap0, fp.swap1, ss.l, cc.l);
-  sp.h = sel2(fp.swap0, fp.swap1, cc.h, ss.h);
-  sp.l = sel2(fp.swap0, fp.swap1, cc.l, ss.l);
   // x = r cos(theta) sin(phi), y = r sin(theta) sin(phi), z = r cos(phi)
   const float2 r = make_float2(r0, r1);
   FF2 R;
@@ -344,7 +375,7 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const TabEntry
   // cos(phi^) < 0 iff its fold reflected; (+0) added so that exact zeros are +0
   X = fma2(x, make_float2(ft.cneg0 ? -1.0f : 1.0f, ft.cneg1 ? -1.0f : 1.0f), bc(0.0f));
   Y = fma2(y, make_float2(copysignf(1.0f, mt.x), copysignf(1.0f, mt.y)), bc(0.0f));
-  Z = fma2(z, make_float2(fp.cneg0 ? -1.0f : 1.0f, fp.cneg1 ? -1.0f : 1.0f), bc(0.0f));
+  Z = fma2(z, make_float2(pneg0 ? -1.0f : 1.0f, pneg1 ? -1.0f : 1.0f), bc(0.0f));
 }
 
 // ----------------------------------------------------------------- encode
@@ -736,13 +767,14 @@ __device__ __forceinline__ void drain(WarpQueue &wq, const DevFormat &F, const T
   __syncwarp();
 }
 
-// Decodes two words through the fast path, falling back per element.
-template <class G>
+// Decodes two words through the fast path, falling back per element.  PT:
+// F.phi_tab holds the per-code phi^ table.
+template <class G, bool PT = true>
 __device__ __forceinline__ void decode2_full(uint64_t w0, uint64_t w1, const DevFormat &F,
                                              const TabEntry *tab_t, const TabEntry *tab_p,
                                              float2 &X, float2 &Y, float2 &Z) {
   bool s0, s1;
-  decode2<G>(w0, w1, tab_t, tab_p, F.Kt_h, F.Kt_l, F.Kp_h, F.Kp_l, X, Y, Z, s0, s1);
+  decode2<G, PT>(w0, w1, F, tab_t, tab_p, X, Y, Z, s0, s1);
   if (s0) {
     const float3 v = decode_generic<G::MAP>(w0, F, tab_t, tab_p);
     X.x = v.x; Y.x = v.y; Z.x = v.z;

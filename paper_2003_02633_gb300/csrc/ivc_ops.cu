@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(256) k_update(const __grid_constant__ DevForma
 // out[i] = encode(op(decode(a[i]), decode(b[i]))) for i in [0, n) by the
 // calling threads: warp `warp` of `nwarps` takes word pairs warp*32 + lane,
 // (warp + nwarps)*32 + lane, ...; the trip count is uniform per warp.  The odd
-// tail element goes to the thread with warp == 0 and lane == 0.
-template <int OP, class G>
+// tail element goes to the thread with warp == 0 and lane == 0.  PT: the
+// format carries the per-code phi^ table (F.phi_tab).
+template <int OP, class G, bool PT = true>
 __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64_t *b, uint64_t *c,
                                                  int64_t n, int64_t warp, int64_t nwarps, int lane,
                                                  float alpha, const DevFormat &F,
@@ -233,8 +234,8 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
       nb = __ldcs(b2 + i + nwarps * 32);
     }
     float2 ux, uy, uz, vx, vy, vz;
-    fast::decode2_full<G>(wa.x, wa.y, F, tab_t, tab_p, ux, uy, uz);
-    fast::decode2_full<G>(wb.x, wb.y, F, tab_t, tab_p, vx, vy, vz);
+    fast::decode2_full<G, PT>(wa.x, wa.y, F, tab_t, tab_p, ux, uy, uz);
+    fast::decode2_full<G, PT>(wb.x, wb.y, F, tab_t, tab_p, vx, vy, vz);
     float2 sx, sy, sz;
     if (OP == IVC_OP_ADD) {
       sx = fast::add2(ux, vx); sy = fast::add2(uy, vy); sz = fast::add2(uz, vz);
@@ -258,12 +259,12 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
   }
 }
 
-template <int OP, class G>
+template <int OP, class G, bool PT>
 __global__ void __launch_bounds__(256, 3) k_fused_fast(const __grid_constant__ DevFormat F,
                                                     const uint64_t *a, const uint64_t *b,
                                                     uint64_t *c, int64_t n, float alpha) {
   IVC_TABLES(F, G::MAP);
-  fused_fast_range<OP, G>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+  fused_fast_range<OP, G, PT>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                        ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t,
                        tab_p, IVC_QUEUE(F));
 }
@@ -655,14 +656,20 @@ cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P
 cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_t *b, uint64_t *c,
                             int64_t n, const LaunchShape &s, cudaStream_t st) {
   return with_geo(F, [&](auto g) {
-    k_fused_fast<IVC_OP_ADD, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n, 0.0f);
+    if (F.phi_tab)
+      k_fused_fast<IVC_OP_ADD, decltype(g), true><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n,
+                                                                                  0.0f);
+    else  // no per-code phi^ table (the allocation-free entry point)
+      k_fused_fast<IVC_OP_ADD, decltype(g), false><<<s.grid, s.block, s.smem, st>>>(F, a, b, c,
+                                                                                   n, 0.0f);
   });
 }
 
 cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
                              int64_t n, const LaunchShape &s, cudaStream_t st) {
   return with_geo(F, [&](auto g) {
-    k_fused_fast<IVC_OP_AXPY, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n, alpha);
+    k_fused_fast<IVC_OP_AXPY, decltype(g), true><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n,
+                                                                                 alpha);
   });
 }
 
@@ -704,8 +711,8 @@ static const void *kernel_ptr(int kind) {
     case K_AXPY: return (const void *)k_axpy<MAP>;
     case K_UPDATE: return (const void *)k_update<MAP>;
     case K_BATCH_ADD: return (const void *)k_batched<MAP, IVC_OP_ADD>;
-    case K_ADD_FAST: return (const void *)k_fused_fast<IVC_OP_ADD, fast::GeoPrimary>;
-    case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY, fast::GeoPrimary>;
+    case K_ADD_FAST: return (const void *)k_fused_fast<IVC_OP_ADD, fast::GeoPrimary, true>;
+    case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY, fast::GeoPrimary, true>;
     case K_UPDATE_FAST: return (const void *)k_update_fast<fast::GeoPrimary>;
     case K_BATCH_ADD_FAST: return (const void *)k_batched_fast<IVC_OP_ADD, fast::GeoPrimary>;
     case K_COMPRESS_FAST: return (const void *)k_compress_fast<fast::GeoPrimary>;
