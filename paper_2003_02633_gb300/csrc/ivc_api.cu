@@ -16,6 +16,9 @@ using namespace ivc;
 namespace {
 
 const long double kPiL = 3.14159265358979323846264338327950288419716939937510L;
+// node counts of the tanh map's encoder tables: |theta| in [0, pi], phi in
+// [0, pi/2] at spacing pi / 1024
+constexpr int kTanhEstT = 1025, kTanhEstP = 513;
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -127,8 +130,34 @@ struct TableKey {
 struct TableSet {
   TabEntry *dev = nullptr;
   size_t n_uniform_t = 0, n_uniform_p = 0, off_phi = 0;
-  size_t off_dec_t = 0, off_dec_p = 0, off_bnd_t = 0, off_bnd_p = 0;
+  size_t off_dec_t = 0, off_dec_p = 0, off_bnd_t = 0, off_bnd_p = 0, off_est = 0;
 };
+
+// Node tables of the tanh map's fast encoder (Sec. 2.5, reading R11): the bin
+// coordinate t(a) = n_max (tanh(g w(a)) + c) / (2c), c = tanh g, with
+// w = a / pi for |theta| = a in [0, pi] (t from n_max / 2 to n_max) and
+// w = 2 a / pi - 1 for phi = a in [0, pi/2] (t from 0 to n_max / 2), at the
+// nodes a = j pi / 1024: floor t, the fraction, t' and t'' / 2 (derivatives
+// in the angle), for a quadratic step to the input angle.
+void tanh_est_table(long double nmax, long double g, bool theta, int nodes,
+                    std::vector<TabEntry> &out) {
+  const long double c = tanhl(g);
+  const long double s = nmax / (2.0L * c);
+  const long double dw = theta ? 1.0L / kPiL : 2.0L / kPiL;  // dw / da
+  for (int j = 0; j < nodes; ++j) {
+    const long double a = kPiL * (long double)j / 1024.0L;
+    const long double w = theta ? a / kPiL : 2.0L * a / kPiL - 1.0L;
+    const long double th = tanhl(g * w);
+    const long double sech2 = 1.0L - th * th;
+    long double t = s * (th + c);
+    if (j == 0) t = theta ? nmax / 2.0L : 0.0L;   // exact end points
+    if (j == nodes - 1) t = theta ? nmax : nmax / 2.0L;
+    const long double ti = floorl(t);
+    const long double d1 = s * g * dw * sech2;
+    const long double d2 = s * g * g * dw * dw * (-2.0L * sech2 * th) / 2.0L;
+    out.push_back(TabEntry{(float)ti, (float)(t - ti), (float)d1, (float)d2});
+  }
+}
 
 // cos, sin of pi k / M for k = 0 .. floor(M / 2): the per-code phi^ table of
 // the fast decoders (exact values at k = 0 and 2k = M).
@@ -184,6 +213,9 @@ ivc_status get_tables(const ivc_format *f, const Geometry &g, int device, TableS
                         : psi_of_t((long double)k + 0.5L, (long double)g.M, gm);
       host.push_back(phi_entry_psi(psi));
     }
+    ts.off_est = host.size();
+    tanh_est_table((long double)g.N, gm, true, kTanhEstT, host);
+    tanh_est_table((long double)g.M, gm, false, kTanhEstP, host);
   } else {
     uniform_table(g.N, host);
     ts.n_uniform_t = host.size();
@@ -265,6 +297,8 @@ ivc_status ivc::format_fields(const ivc_format *f, DevFormat *F, int *map_out) {
     F->tanh_c = (float)tanhl((long double)f->gamma);
     F->tanh_inv2c = (float)(1.0L / (2.0L * tanhl((long double)f->gamma)));
     F->nent_t = F->nent_p = 0;
+    F->nest_t = kTanhEstT;
+    F->nest_p = kTanhEstP;
   }
   *map_out = f->map;
   return IVC_OK;
@@ -292,6 +326,7 @@ ivc_status make_devformat(const ivc_format *f, DevFormat *F, int *map_out) {
     F->dec_p = ts.dev + ts.off_dec_p;
     F->bnd_t = ts.dev + ts.off_bnd_t;
     F->bnd_p = ts.dev + ts.off_bnd_p;
+    F->est_tab = ts.dev + ts.off_est;
   }
   return IVC_OK;
 }

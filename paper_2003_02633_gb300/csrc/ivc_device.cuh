@@ -89,6 +89,11 @@ struct DevFormat {
   float gam, tanh_c, tanh_inv2c;    // gamma, c = tanh(gamma), 1 / (2c)
   const TabEntry *dec_t, *dec_p;    // cos/sin of theta^_n (N+1), phi^_n (M+1)
   const TabEntry *bnd_t, *bnd_p;    // cos/sin at boundaries k + 1/2 (N, M)
+  // tanh companding, fast encoder: bin coordinate t at nodes j pi / 1024 of
+  // |theta| in [0, pi] (nest_t entries) and of phi in [0, pi/2] (nest_p):
+  // (floor t, t - floor t, dt/dangle, d2t/dangle2 / 2) per node
+  const TabEntry *est_tab;
+  int32_t nest_t, nest_p;
 };
 
 // --------------------------------------------------------------------------

@@ -12,7 +12,7 @@
 //     below 0.0035 bin in t) and runs the error-free side-of-boundary test only
 //     for coordinates within kEps of a rounding boundary, deferred to a
 //     per-warp queue;
-//   * vectors outside |x|_inf in [2^-32, 2^32] (zero, NaN, Inf, tiny, huge) and
+//   * vectors with |x|^2 outside [2^-64, 2^64) (zero, NaN, Inf, tiny, huge) and
 //     non-finite words take the generic code, off the common path.
 #pragma once
 #include "ivc_device.cuh"
@@ -23,6 +23,9 @@ namespace fast {
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
 constexpr float kEps = 0.005f;      // bin-coordinate estimate error bound (with margin)
+// the tanh map's estimate: the atan error scaled by the map's largest slope
+// relative to the uniform map, gamma / tanh(gamma) <= 1.32 for gamma <= 1
+constexpr float kEpsTanh = 0.0065f;
 
 // The layouts this path serves: grid sizes n_theta_max = N, n_phi_max = M,
 // head-table steps 2^ST (theta grid pi m / N) and 2^SP (phi grid
@@ -130,6 +133,32 @@ struct GeoL1617 {
   }
 };
 
+// <0,7,22>-17-18 with the tanh companding map (Sec. 2.5) on both angles:
+// the bit layout of GeoPrimary; the decoder reads cos/sin of every code's
+// angle from per-code tables (global), the encoder interpolates the bin
+// coordinate from node tables (shared memory) and decides against the
+// per-boundary tables.  Format parameter gamma in (0, 1].
+struct GeoTanh {
+  static constexpr int N = 262143, M = 131071;
+  static constexpr int ST = 8, SP = 8, NT = 0, NP = 0;
+  static constexpr int MAP = MAP_TANH;
+  static constexpr float CTH = 0.0f, CTL = 0.0f, CPH = 0.0f, CPL = 0.0f;  // unused
+  static constexpr uint32_t EALL = 127u;
+  __device__ static uint32_t efield(uint32_t hi) { return hi >> 25; }
+  __device__ static float mag(uint32_t hi) {
+    return __uint_as_float(((hi >> 2) & 0xFFFFFFFEu) + (47u << 23));
+  }
+  __device__ static uint32_t hi_of(uint32_t rb) { return ((rb - (47u << 23)) << 2) & 0xFFFFFFF8u; }
+  __device__ static void unpack(uint32_t hi, uint32_t lo, uint32_t &nt, uint32_t &np) {
+    nt = lo & 0x3FFFFu;
+    np = __funnelshift_r(lo, hi, 18) & 0x1FFFFu;
+  }
+  __device__ static uint64_t pack(uint32_t hi_mag, int np, int nt) {
+    return ((uint64_t)(hi_mag | ((uint32_t)np >> 14)) << 32) |
+           (((uint32_t)np << 18) | (uint32_t)nt);
+  }
+};
+
 // Field positions of each fast layout, checked against a format.
 template <class G> struct GeoFields;
 template <> struct GeoFields<GeoPrimary> {
@@ -148,6 +177,10 @@ template <> struct GeoFields<GeoL1617> {
   static constexpr uint32_t sh_phi = 17, sh_m = 33, sh_e = 56, mask_e = 255, mask_m = 0x7FFFFF;
   static constexpr int e_off = 0;
 };
+template <> struct GeoFields<GeoTanh> {
+  static constexpr uint32_t sh_phi = 18, sh_m = 35, sh_e = 57, mask_e = 127, mask_m = 0x3FFFFF;
+  static constexpr int e_off = -47;
+};
 
 template <class G>
 __host__ __device__ inline bool is_geo(const DevFormat &F) {
@@ -159,12 +192,14 @@ __host__ __device__ inline bool is_geo(const DevFormat &F) {
 }
 
 // Which fast layout a format is: 1 primary, 2 fractional split, 3
-// <0,7,23>-17-17, 4 <0,8,23>-16-17, 0 none.
+// <0,7,23>-17-17, 4 <0,8,23>-16-17, 5 the primary layout with the tanh map,
+// 0 none.
 __host__ __device__ inline int fast_geometry(int map, const DevFormat &F) {
   if (map == MAP_UNIFORM && is_geo<GeoPrimary>(F)) return 1;
   if (map == MAP_FRACSPLIT && is_geo<GeoSplit>(F)) return 2;
   if (map == MAP_UNIFORM && is_geo<GeoL1717>(F)) return 3;
   if (map == MAP_UNIFORM && is_geo<GeoL1617>(F)) return 4;
+  if (map == MAP_TANH && is_geo<GeoTanh>(F) && F.gam > 0.0f && F.gam <= 1.0f) return 5;
   return 0;
 }
 
@@ -283,6 +318,16 @@ __device__ __forceinline__ void prod3(FF2 R, FF2 a, float2 &P, float2 &T) {
 
 __device__ __forceinline__ float apply_neg(float v, bool n) { return (n && v != 0.0f) ? -v : v; }
 
+// Magnitude of a signed float-float pair (the tail keeps its sign relative to
+// the head) and the head's sign as +-1.
+__device__ __forceinline__ FF2 abs_ff2(float2 h, float2 l, float2 &sg) {
+  sg = make_float2(copysignf(1.0f, h.x), copysignf(1.0f, h.y));
+  FF2 m;
+  m.h = mul2(h, sg);
+  m.l = mul2(l, sg);
+  return m;
+}
+
 // cos and sin (float-float magnitudes) of phi^ = pi n / M for both elements,
 // and whether cos phi^ is negative.  PT: one 16-byte load per element from
 // the per-code table of k = min(n, M - n) (cos(pi - a) = -cos a, sin(pi -
@@ -339,24 +384,42 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const DevForma
   uint32_t nt0, np0, nt1, np1;
   G::unpack(hi0, lo0, nt0, np0);
   G::unpack(hi1, lo1, nt1, np1);
-  // phi^ first: with the per-code table its loads are in flight while theta^
-  // is evaluated
-  FF2 cp, sp;
-  bool pneg0, pneg1;
-  phi_pair<G, PT>(np0, np1, F, tab_p, cp, sp, pneg0, pneg1);
-  const float2 ntf = add2(make_float2(__uint_as_float(nt0 | 0x4B000000u),
-                                      __uint_as_float(nt1 | 0x4B000000u)),
-                          bc(-8388608.0f));
-  // theta^ = pi (2 n_theta - N) / N
-  const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)G::N));
-  const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)G::N);
-  FF2 cc, ss;
-  sincos2<G::ST>(ft.b, tab_t, F.Kt_h, F.Kt_l, cc, ss);
-  FF2 ct, st;
-  ct.h = sel2(ft.swap0, ft.swap1, ss.h, cc.h);
-  ct.l = sel2(ft.swap0, ft.swap1, ss.l, cc.l);
-  st.h = sel2(ft.swap0, ft.swap1, cc.h, ss.h);
-  st.l = sel2(ft.swap0, ft.swap1, cc.l, ss.l);
+  FF2 ct, st, cp, sp;
+  float2 sgx, sgy, sgz;  // signs of cos(theta^), sin(theta^), cos(phi^) as +-1
+  if constexpr (G::MAP == MAP_TANH) {
+    // signed float-float cos/sin of every code's angle, read through L2
+    const float4 *dt = reinterpret_cast<const float4 *>(F.dec_t);
+    const float4 *dp = reinterpret_cast<const float4 *>(F.dec_p);
+    const float4 a0 = __ldg(dt + nt0), a1 = __ldg(dt + nt1);
+    const float4 b0 = __ldg(dp + np0), b1 = __ldg(dp + np1);
+    ct = abs_ff2(make_float2(a0.x, a1.x), make_float2(a0.y, a1.y), sgx);
+    st = abs_ff2(make_float2(a0.z, a1.z), make_float2(a0.w, a1.w), sgy);
+    cp = abs_ff2(make_float2(b0.x, b1.x), make_float2(b0.y, b1.y), sgz);
+    sp.h = make_float2(b0.z, b1.z);  // sin(phi^) >= 0
+    sp.l = make_float2(b0.w, b1.w);
+  } else {
+    // phi^ first: with the per-code table its loads are in flight while
+    // theta^ is evaluated
+    bool pneg0, pneg1;
+    phi_pair<G, PT>(np0, np1, F, tab_p, cp, sp, pneg0, pneg1);
+    const float2 ntf = add2(make_float2(__uint_as_float(nt0 | 0x4B000000u),
+                                        __uint_as_float(nt1 | 0x4B000000u)),
+                            bc(-8388608.0f));
+    // theta^ = pi (2 n_theta - N) / N
+    const float2 mt = fma2(ntf, bc(2.0f), bc(-(float)G::N));
+    const Fold2 ft = fold2(make_float2(fabsf(mt.x), fabsf(mt.y)), (float)G::N);
+    FF2 cc, ss;
+    sincos2<G::ST>(ft.b, tab_t, F.Kt_h, F.Kt_l, cc, ss);
+    ct.h = sel2(ft.swap0, ft.swap1, ss.h, cc.h);
+    ct.l = sel2(ft.swap0, ft.swap1, ss.l, cc.l);
+    st.h = sel2(ft.swap0, ft.swap1, cc.h, ss.h);
+    st.l = sel2(ft.swap0, ft.swap1, cc.l, ss.l);
+    // cos(theta^) < 0 iff the fold reflected, sin(theta^) < 0 iff m < 0,
+    // cos(phi^) < 0 iff n_phi > M / 2
+    sgx = make_float2(ft.cneg0 ? -1.0f : 1.0f, ft.cneg1 ? -1.0f : 1.0f);
+    sgy = make_float2(copysignf(1.0f, mt.x), copysignf(1.0f, mt.y));
+    sgz = make_float2(pneg0 ? -1.0f : 1.0f, pneg1 ? -1.0f : 1.0f);
+  }
   // x = r cos(theta) sin(phi), y = r sin(theta) sin(phi), z = r cos(phi)
   const float2 r = make_float2(r0, r1);
   FF2 R;
@@ -371,11 +434,10 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const DevForma
   const float2 z = ru_pair(P, T, a0, a1);
   slow0 |= a0;
   slow1 |= a1;
-  // signs: cos(theta^) < 0 iff the fold reflected, sin(theta^) < 0 iff m < 0,
-  // cos(phi^) < 0 iff its fold reflected; (+0) added so that exact zeros are +0
-  X = fma2(x, make_float2(ft.cneg0 ? -1.0f : 1.0f, ft.cneg1 ? -1.0f : 1.0f), bc(0.0f));
-  Y = fma2(y, make_float2(copysignf(1.0f, mt.x), copysignf(1.0f, mt.y)), bc(0.0f));
-  Z = fma2(z, make_float2(pneg0 ? -1.0f : 1.0f, pneg1 ? -1.0f : 1.0f), bc(0.0f));
+  // signs; (+0) added so that exact zeros are +0
+  X = fma2(x, sgx, bc(0.0f));
+  Y = fma2(y, sgy, bc(0.0f));
+  Z = fma2(z, sgz, bc(0.0f));
 }
 
 // ----------------------------------------------------------------- encode
@@ -452,13 +514,61 @@ __device__ __forceinline__ BinCoord2 bin_coord2(float2 K0, float2 s1, float2 bh,
   return c;
 }
 
+// pi, pi / 2 and pi / 1024 as float-float head + tail; 1024 / pi
+constexpr float kPiH = 0x1.921fb6p+1f, kPiL = -0x1.777a5cp-24f;
+constexpr float kPi2H = 0x1.921fb6p+0f, kPi2L = -0x1.777a5cp-25f;
+constexpr float kNodeH = 0x1.921fb6p-9f, kNodeL = -0x1.777a5cp-34f;
+constexpr float kNodeScale = 0x1.45f306p+8f;
+constexpr int kTanhNodesT = 1025, kTanhNodesP = 513;  // nodes over [0, pi] and [0, pi/2]
+
+// tanh map (Sec. 2.5): bin coordinate t(a) at the angle a = Ka + sa (bh +
+// bl) (Ka in {0, pi/2, pi} in float-float, beta = bh + bl <= pi / 4 as
+// atan_ratio2 returns it) from the
+// nearest node j pi / 1024 of `tab` (nodes entries: floor t_j, t_j - floor
+// t_j, t'_j, t''_j / 2) by the quadratic step t_j + t' d + t''/2 d^2, d =
+// a - j pi / 1024 (|d| <= pi / 2048: the cubic term is below 1e-4 bin for
+// gamma <= 1).  Returns floor t and t - floor t (within 1e-4 bin of the
+// exact bin coordinate of a).
+__device__ __forceinline__ BinCoord2 tanh_bin2(float2 Kah, float2 Kal, float2 sa, float2 bh,
+                                               float2 bl, const TabEntry *__restrict__ tab,
+                                               int nodes) {
+  // beta = bh + bl with bl up to a fifth of bh (atan_ratio2's q and its
+  // correction): renormalised to a head and a tail (Fast2Sum, |bh| >= |bl|)
+  const float2 gh = add2(bh, bl);
+  const float2 gl = add2(sub2(bh, gh), bl);
+  // a = ah + al: Fast2Sum of Kah and sa gh (|Kah| >= gh unless Kah = 0),
+  // then the tails
+  const float2 ah = fma2(sa, gh, Kah);
+  const float2 al = add2(fma2(sa, gh, sub2(Kah, ah)), fma2(sa, gl, Kal));
+  // nearest node (magic-number rounding of a 1024 / pi), kept in range
+  const float2 jb = fma2(ah, bc(kNodeScale), bc(kMagic));
+  const uint32_t j0 = min(__float_as_uint(jb.x) - kMagicBits, (uint32_t)(nodes - 1));
+  const uint32_t j1 = min(__float_as_uint(jb.y) - kMagicBits, (uint32_t)(nodes - 1));
+  const float2 jf = make_float2((float)j0, (float)j1);
+  const TabEntry e0 = tab[j0];
+  const TabEntry e1 = tab[j1];
+  // d = a - j pi / 1024: the head difference is exact up to one rounding of
+  // a value below 2^-9
+  const float2 d = add2(fma2(jf, bc(-kNodeH), ah), fma2(jf, bc(-kNodeL), al));
+  const float2 f = fma2(fma2(make_float2(e0.sl, e1.sl), d, make_float2(e0.sh, e1.sh)), d,
+                        make_float2(e0.cl, e1.cl));
+  const float2 ff = floor2(f);
+  BinCoord2 c;
+  c.fl = add2(make_float2(e0.ch, e1.ch), ff);
+  c.fr = sub2(f, ff);
+  return c;
+}
+
 struct Est2 {
   float2 fl_t, fr_t;   // theta: t = (N - 1) / 2 + h, h = w + 1/2 (floor of h, frac)
   float2 fl_p, fr_p;   // phi:   t directly
 };
 
+// tab_t_est / tab_p_est: the tanh map's node tables (unused otherwise).
 template <class G>
-__device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r2h, float2 r2l) {
+__device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r2h, float2 r2l,
+                                          const TabEntry *__restrict__ tab_t_est,
+                                          const TabEntry *__restrict__ tab_p_est) {
   constexpr int kN = G::N, kM = G::M;
   Est2 e;
   // theta = atan2(y, x); t = N/2 + w, h = w + 1/2 = K0 + 1/2 + s1 g,
@@ -471,6 +581,20 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
     // psi = beta (|x| >= |y|) or pi/2 - beta; theta = +-psi (x >= 0) or +-(pi - psi)
     const bool u0 = ay0 > ax0, u1 = ay1 > ax1;
     const bool v0 = x.x < 0.0f, v1 = x.y < 0.0f;
+    if constexpr (G::MAP == MAP_TANH) {
+      // |theta| = Ka + sa beta: Ka = pi/2 (u), pi (v, not u) or 0; sa = -1
+      // when u != v; t(theta) = N - t(|theta|) for y < 0 (or -0), the map
+      // being odd about theta = 0
+      const float2 Kah = make_float2(u0 ? kPi2H : (v0 ? kPiH : 0.0f), u1 ? kPi2H : (v1 ? kPiH : 0.0f));
+      const float2 Kal = make_float2(u0 ? kPi2L : (v0 ? kPiL : 0.0f), u1 ? kPi2L : (v1 ? kPiL : 0.0f));
+      const float2 sa = make_float2((u0 != v0) ? -1.0f : 1.0f, (u1 != v1) ? -1.0f : 1.0f);
+      const BinCoord2 c = tanh_bin2(Kah, Kal, sa, bh, bl, tab_t_est, kTanhNodesT);
+      const bool m0 = signbit(y.x), m1 = signbit(y.y);
+      // floor t relative to (N - 1) / 2, as the uniform branch returns it
+      e.fl_t = make_float2(m0 ? (float)((kN - 1) / 2) - c.fl.x : c.fl.x - (float)((kN - 1) / 2),
+                           m1 ? (float)((kN - 1) / 2) - c.fl.y : c.fl.y - (float)((kN - 1) / 2));
+      e.fr_t = make_float2(m0 ? 1.0f - c.fr.x : c.fr.x, m1 ? 1.0f - c.fr.y : c.fr.y);
+    } else {
     // u: psi = pi/2 - beta (offset N/4, sign -); v: pi - psi (offset N/2 - ., sign
     // flips); y < 0 (or -0): theta = -(.) (offset and sign flip)
     float2 K0 = make_float2(u0 ? 0.25f * (float)kN : 0.0f, u1 ? 0.25f * (float)kN : 0.0f);
@@ -485,6 +609,7 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
     const BinCoord2 c = bin_coord2(add2(K0, bc(0.5f)), s1, bh, bl, G::CTH, G::CTL);
     e.fl_t = c.fl;
     e.fr_t = c.fr;
+    }
   }
   // phi = atan2(rho, z); t = K0 + s1 g, g = M beta / pi
   {
@@ -501,6 +626,17 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
                 make_float2(fmaxf(az0, rho0), fmaxf(az1, rho1)), bh, bl);
     const bool u0 = rho0 > az0, u1 = rho1 > az1;
     const bool n0 = z.x < 0.0f, n1 = z.y < 0.0f;
+    if constexpr (G::MAP == MAP_TANH) {
+      // phi' = min(phi, pi - phi) = pi/2 - beta (rho > |z|) or beta; t(phi) =
+      // M - t(phi') for z < 0, the map being odd about phi = pi/2
+      const float2 Kah = make_float2(u0 ? kPi2H : 0.0f, u1 ? kPi2H : 0.0f);
+      const float2 Kal = make_float2(u0 ? kPi2L : 0.0f, u1 ? kPi2L : 0.0f);
+      const float2 sa = make_float2(u0 ? -1.0f : 1.0f, u1 ? -1.0f : 1.0f);
+      const BinCoord2 c = tanh_bin2(Kah, Kal, sa, bh, bl, tab_p_est, kTanhNodesP);
+      e.fl_p = make_float2(n0 ? (float)(kM - 1) - c.fl.x : c.fl.x,
+                           n1 ? (float)(kM - 1) - c.fl.y : c.fl.y);
+      e.fr_p = make_float2(n0 ? 1.0f - c.fr.x : c.fr.x, n1 ? 1.0f - c.fr.y : c.fr.y);
+    } else {
     // |z| >= rho: t = g (z >= 0) or M - g;  rho > |z|: t = M/2 -+ g
     const float2 K0 = make_float2(u0 ? 0.5f * (float)kM : (n0 ? (float)kM : 0.0f),
                                   u1 ? 0.5f * (float)kM : (n1 ? (float)kM : 0.0f));
@@ -508,6 +644,7 @@ __device__ __forceinline__ Est2 estimate2(float2 x, float2 y, float2 z, float2 r
     const BinCoord2 c = bin_coord2(K0, s1, bh, bl, G::CPH, G::CPL);
     e.fl_p = c.fl;
     e.fr_p = c.fr;
+    }
   }
   return e;
 }
@@ -521,11 +658,18 @@ __device__ __forceinline__ int exact_side(int kind, int k, float xs, float ys, f
                                           const TabEntry *tab_p) {
   const bool ph = kind != 0;
   FF c, s;
-  bool cn, sn;
-  sincospi_grid(ph ? 2 * k + 1 : 2 * k + 1 - F.N, ph ? F.Dp : F.Dt, ph ? tab_p : tab_t,
-                ph ? F.sp : F.st, ph ? F.Kp_h : F.Kt_h, ph ? F.Kp_l : F.Kt_l, c, s, cn, sn);
-  c = neg_if(c, cn);
-  s = neg_if(s, sn);
+  if constexpr (G::MAP == MAP_TANH) {
+    // signed cos/sin of the boundary angle from the per-boundary tables
+    const TabEntry e = ph ? F.bnd_p[k] : F.bnd_t[k];
+    c = FF{e.ch, e.cl};
+    s = FF{e.sh, e.sl};
+  } else {
+    bool cn, sn;
+    sincospi_grid(ph ? 2 * k + 1 : 2 * k + 1 - F.N, ph ? F.Dp : F.Dt, ph ? tab_p : tab_t,
+                  ph ? F.sp : F.st, ph ? F.Kp_h : F.Kt_h, ph ? F.Kp_l : F.Kt_l, c, s, cn, sn);
+    c = neg_if(c, cn);
+    s = neg_if(s, sn);
+  }
   // theta: sign(y cos - x sin);  phi: sign(rho cos - z sin)
   float a = ys, a_l = 0.0f;
   if (ph) {
@@ -583,14 +727,6 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
                                         const TabEntry *__restrict__ tab_p) {
   constexpr int kN = G::N, kM = G::M;
   Enc2 r;
-  // |x|_inf in [2^-32, 2^32): no scaling, no range limits, no specials
-  // (integer max of the magnitude bits: NaN compares above every finite value)
-  const uint32_t am0 = max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(y.x) & 0x7fffffffu),
-                           __float_as_uint(z.x) & 0x7fffffffu);
-  const uint32_t am1 = max(max(__float_as_uint(x.y) & 0x7fffffffu, __float_as_uint(y.y) & 0x7fffffffu),
-                           __float_as_uint(z.y) & 0x7fffffffu);
-  const bool gen0 = !((am0 - 0x2F800000u) < 0x20000000u);
-  const bool gen1 = !((am1 - 0x2F800000u) < 0x20000000u);
   // squares and sums in float-float
   const float2 px = mul2(x, x), ex = fma2(x, x, neg2(px));
   const float2 py = mul2(y, y), ey = fma2(y, y, neg2(py));
@@ -601,6 +737,10 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   const float2 sh = add2(r2h, pz);
   t = sub2(sh, r2h);
   const float2 sl = add2(add2(sub2(r2h, sub2(sh, t)), sub2(pz, t)), add2(r2l, ez));
+  // |x|^2 in [2^-64, 2^64): NaN, Inf, the zero vector and magnitudes the
+  // fast path does not serve fail the test
+  const bool gen0 = !(sh.x >= 0x1p-64f && sh.x < 0x1p64f);
+  const bool gen1 = !(sh.y >= 0x1p-64f && sh.y < 0x1p64f);
   // float-float square root, RN32
   const float2 y0 = make_float2(rsqrtf(sh.x), rsqrtf(sh.y));
   const float2 hy0 = mul2(y0, bc(0.5f));
@@ -621,7 +761,7 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   // the queue like the out-of-window vectors
   const bool gq0 = gen0 || nslow0, gq1 = gen1 || nslow1;
   // angle estimates
-  const Est2 e = estimate2<G>(x, y, z, r2h, r2l);
+  const Est2 e = estimate2<G>(x, y, z, r2h, r2l, tab_t, tab_p);
   // k = floor(t) clamped to [0, n_max - 1]; the fraction absorbs the clamp
   // (t = n_max gives fraction 1, t < 0 a negative one: never flagged)
   float2 ft = add2(e.fl_t, bc((float)((kN - 1) / 2)));
@@ -639,8 +779,9 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   int np0 = kp0 + (frp.x >= 0.5f ? 1 : 0), np1 = kp1 + (frp.y >= 0.5f ? 1 : 0);
   // pending exact decisions: kinds within kEps of a rounding boundary
   // (bit 0 theta, bit 1 phi); their words are provisional
-  r.pend0 = gq0 ? 4u : (fabsf(frt.x - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= kEps ? 2u : 0u);
-  r.pend1 = gq1 ? 4u : (fabsf(frt.y - 0.5f) <= kEps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= kEps ? 2u : 0u);
+  constexpr float eps = G::MAP == MAP_TANH ? kEpsTanh : kEps;
+  r.pend0 = gq0 ? 4u : (fabsf(frt.x - 0.5f) <= eps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= eps ? 2u : 0u);
+  r.pend1 = gq1 ? 4u : (fabsf(frt.y - 0.5f) <= eps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= eps ? 2u : 0u);
   r.nt0 = (r.pend0 & 1u) ? kt0 : nt0;
   r.nt1 = (r.pend1 & 1u) ? kt1 : nt1;
   r.np0 = (r.pend0 & 2u) ? kp0 : np0;
@@ -783,6 +924,25 @@ __device__ __forceinline__ void decode2_full(uint64_t w0, uint64_t w1, const Dev
     const float3 v = decode_generic<G::MAP>(w1, F, tab_t, tab_p);
     X.y = v.x; Y.y = v.y; Z.y = v.z;
   }
+}
+
+// Shared-memory tables of the fast kernels: the uniform head tables, or for
+// the tanh map the encoder's node tables; the deferred-test queues follow.
+template <class G>
+__host__ __device__ __forceinline__ int fast_ntab_t(const DevFormat &F) {
+  return G::MAP == MAP_TANH ? F.nest_t : F.nent_t;
+}
+template <class G>
+__host__ __device__ __forceinline__ int fast_ntab(const DevFormat &F) {
+  return G::MAP == MAP_TANH ? F.nest_t + F.nest_p : F.nent_t + F.nent_p;
+}
+template <class G>
+__device__ __forceinline__ void stage_fast_tables(const DevFormat &F, TabEntry *smem) {
+  const float4 *src = reinterpret_cast<const float4 *>(G::MAP == MAP_TANH ? F.est_tab : F.tab);
+  float4 *dst = reinterpret_cast<float4 *>(smem);
+  const int total = fast_ntab<G>(F);
+  for (int i = threadIdx.x; i < total; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
 }
 
 }  // namespace fast

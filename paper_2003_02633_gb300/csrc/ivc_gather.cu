@@ -112,6 +112,7 @@ cudaError_t launch_gather(int map, const DevFormat &F, const uint64_t *w, int64_
       k_gather_fast<decltype(g)><<<grid, 256, smem, st>>>(F, w, nw, idx, n, xyz);
       return cudaGetLastError();
     };
+    if (fast::is_geo<fast::GeoTanh>(F)) return run(fast::GeoTanh{});
     if (fast::is_geo<fast::GeoSplit>(F)) return run(fast::GeoSplit{});
     if (fast::is_geo<fast::GeoL1717>(F)) return run(fast::GeoL1717{});
     if (fast::is_geo<fast::GeoL1617>(F)) return run(fast::GeoL1617{});

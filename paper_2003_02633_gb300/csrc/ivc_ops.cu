@@ -6,6 +6,8 @@
 // cache hints when the pointers are 16-byte aligned; the trigonometric head
 // tables of the uniform grids are staged once per block into shared memory.
 // Grids are persistent-style grid-stride loops sized from the SM count.
+#include <type_traits>
+
 #include "ivc_internal.h"
 
 namespace ivc {
@@ -16,8 +18,14 @@ namespace ivc {
   const TabEntry *tab_t = ivc_smem_tab;                           \
   const TabEntry *tab_p = ivc_smem_tab + (MAP == MAP_TANH ? 0 : F.nent_t)
 
-// Deferred-test queues of the fast kernels: shared memory after the tables.
-#define IVC_QUEUE(F) ((void *)(ivc_smem_tab + (F).nent_t + (F).nent_p))
+// Tables of the fast kernels of layout G (the tanh map: the encoder's node
+// tables) and their queues.
+#define IVC_FAST_TABLES(F, G)                                     \
+  extern __shared__ TabEntry ivc_smem_tab[];                      \
+  fast::stage_fast_tables<G>(F, ivc_smem_tab);                    \
+  const TabEntry *tab_t = ivc_smem_tab;                           \
+  const TabEntry *tab_p = ivc_smem_tab + fast::fast_ntab_t<G>(F)
+#define IVC_FAST_QUEUE(F, G) ((void *)(ivc_smem_tab + fast::fast_ntab<G>(F)))
 
 // Per-thread range-event counters (overflow, underflow, NaN).
 using Events = fast::Events;
@@ -263,10 +271,10 @@ template <int OP, class G, bool PT>
 __global__ void __launch_bounds__(256, 3) k_fused_fast(const __grid_constant__ DevFormat F,
                                                     const uint64_t *a, const uint64_t *b,
                                                     uint64_t *c, int64_t n, float alpha) {
-  IVC_TABLES(F, G::MAP);
+  IVC_FAST_TABLES(F, G);
   fused_fast_range<OP, G, PT>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                        ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t,
-                       tab_p, IVC_QUEUE(F));
+                       tab_p, IVC_FAST_QUEUE(F, G));
 }
 
 // Compress n AoS vectors (primary layout), two per thread; counts as in
@@ -275,14 +283,14 @@ template <class G>
 __global__ void __launch_bounds__(256, 3) k_compress_fast(const __grid_constant__ DevFormat F,
                                                        const float *__restrict__ xyz, int64_t n,
                                                        uint64_t *w, ivc_counts *counts) {
-  IVC_TABLES(F, G::MAP);
+  IVC_FAST_TABLES(F, G);
   const int64_t n2 = n >> 1;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float2 *v2 = reinterpret_cast<const float2 *>(xyz);
   ulonglong2 *w2 = reinterpret_cast<ulonglong2 *>(w);
-  fast::WarpQueue wq = fast::warp_queue(IVC_QUEUE(F));
+  fast::WarpQueue wq = fast::warp_queue(IVC_FAST_QUEUE(F, G));
   Events ev;
   // floats 6i .. 6i+5: x0 y0 z0 x1 y1 z1; the next iteration's are loaded
   // before this iteration's arithmetic
@@ -324,7 +332,7 @@ template <class G>
 __global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__ DevFormat F,
                                                          const uint64_t *__restrict__ w,
                                                          int64_t n, float *xyz) {
-  IVC_TABLES(F, G::MAP);
+  IVC_FAST_TABLES(F, G);
   const int64_t n2 = n >> 1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(w);
@@ -335,7 +343,9 @@ __global__ void __launch_bounds__(256) k_decompress_fast(const __grid_constant__
     const ulonglong2 ww = nw;
     if (i + stride < n2) nw = __ldcs(w2 + i + stride);
     float2 X, Y, Z;
-    fast::decode2_full<G>(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z);
+    // table-free decode: a launch of decodes alone is faster with the phi^
+    // head table in shared memory than with the per-code table (measured)
+    fast::decode2_full<G, false>(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z);
     __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
     __stcs(v2 + 3 * i + 1, make_float2(Z.x, X.y));
     __stcs(v2 + 3 * i + 2, make_float2(Y.y, Z.y));
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(256, 3) k_update_fast(const __grid_constant__ 
                                                      const uint64_t *v, const uint64_t *f,
                                                      const float *__restrict__ rho,
                                                      uint64_t *v_out, uint64_t *m_out, int64_t n) {
-  IVC_TABLES(F, G::MAP);
+  IVC_FAST_TABLES(F, G);
   const bool want_m = (rho != nullptr) && (m_out != nullptr);
   const int64_t n2 = n >> 1;
   const int lane = threadIdx.x & 31;
@@ -365,7 +375,7 @@ __global__ void __launch_bounds__(256, 3) k_update_fast(const __grid_constant__ 
   const ulonglong2 *f2 = reinterpret_cast<const ulonglong2 *>(f);
   ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(v_out);
   ulonglong2 *m2 = reinterpret_cast<ulonglong2 *>(m_out);
-  fast::WarpQueue wq = fast::warp_queue(IVC_QUEUE(F));
+  fast::WarpQueue wq = fast::warp_queue(IVC_FAST_QUEUE(F, G));
   ulonglong2 nv = make_ulonglong2(0ull, 0ull), nf = nv;  // next iteration's words
   if (warp * 32 + lane < n2) {
     nv = __ldcs(v2 + warp * 32 + lane);
@@ -468,7 +478,7 @@ __global__ void __launch_bounds__(256) k_batched(const __grid_constant__ DevForm
 template <int OP, class G>
 __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ DevFormat F,
                                                       const __grid_constant__ PlanDev P) {
-  IVC_TABLES(F, G::MAP);
+  IVC_FAST_TABLES(F, G);
   __shared__ long long s_tile;
   uint32_t flags = 0;
   bool done = false;
@@ -502,7 +512,7 @@ __global__ void __launch_bounds__(256) k_batched_fast(const __grid_constant__ De
                         reinterpret_cast<uintptr_t>(c)) & 15u) == 0;
     if (vec2) {
       fused_fast_range<OP, G>(a, b, c, len, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31,
-                           fd.alpha, F, tab_t, tab_p, IVC_QUEUE(F));
+                           fd.alpha, F, tab_t, tab_p, IVC_FAST_QUEUE(F, G));
     } else if (OP == IVC_OP_ADD) {
       fused_range<G::MAP>(a, b, c, len, false, threadIdx.x, blockDim.x, OpAdd{}, F, tab_t,
                           tab_p, flags);
@@ -537,8 +547,12 @@ size_t kernel_smem_bytes(const DevFormat &F, int map, int kind, int block) {
   const bool queue = kind == K_ADD_FAST || kind == K_AXPY_FAST || kind == K_UPDATE_FAST ||
                      kind == K_BATCH_ADD_FAST || kind == K_BATCH_AXPY_FAST ||
                      kind == K_COMPRESS_FAST;
-  return table_smem_bytes(F, map) +
-         (queue ? (size_t)(block / 32) * fast::kQueueCap * sizeof(fast::PendItem) : 0);
+  const bool fastk = queue || kind == K_DECOMPRESS_FAST;
+  // the fast kernels of the tanh map stage the encoder's node tables
+  const size_t tabs = (fastk && map == MAP_TANH)
+                          ? (size_t)(F.nest_t + F.nest_p) * sizeof(TabEntry)
+                          : table_smem_bytes(F, map);
+  return tabs + (queue ? (size_t)(block / 32) * fast::kQueueCap * sizeof(fast::PendItem) : 0);
 }
 
 #define IVC_DISPATCH_MAP(map, KERNEL, ...)                                                    \
@@ -614,9 +628,24 @@ cudaError_t launch_update(int map, const DevFormat &F, float dt, const uint64_t 
 
 // Fast launchers: the layout is read from F (the caller has checked
 // fast::fast_geometry()); f receives a value of the layout's type.
+// Dynamic shared memory above the 48 KB every kernel may use by default needs
+// the kernel's opt-in (the tanh map's fast kernels: node tables and queues).
+__host__ inline cudaError_t allow_smem(const void *kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+#define IVC_LAUNCH(KERNEL, ...)                                                         \
+  do {                                                                                  \
+    if (allow_smem((const void *)KERNEL, s.smem) != cudaSuccess) return;                \
+    KERNEL<<<s.grid, s.block, s.smem, st>>>(__VA_ARGS__);                               \
+  } while (0)
+
 template <class Fn>
 cudaError_t with_geo(const DevFormat &F, Fn f) {
-  if (fast::is_geo<fast::GeoSplit>(F))
+  if (fast::is_geo<fast::GeoTanh>(F))
+    f(fast::GeoTanh{});
+  else if (fast::is_geo<fast::GeoSplit>(F))
     f(fast::GeoSplit{});
   else if (fast::is_geo<fast::GeoL1717>(F))
     f(fast::GeoL1717{});
@@ -632,9 +661,9 @@ cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P
   if (fast::fast_geometry(map, F) != 0) {
     return with_geo(F, [&](auto g) {
       if (op == IVC_OP_ADD)
-        k_batched_fast<IVC_OP_ADD, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, P);
+        IVC_LAUNCH((k_batched_fast<IVC_OP_ADD, decltype(g)>), F, P);
       else
-        k_batched_fast<IVC_OP_AXPY, decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, P);
+        IVC_LAUNCH((k_batched_fast<IVC_OP_AXPY, decltype(g)>), F, P);
     });
   }
   if (op == IVC_OP_ADD) {
@@ -656,34 +685,31 @@ cudaError_t launch_batched(int map, int op, const DevFormat &F, const PlanDev &P
 cudaError_t launch_add_fast(const DevFormat &F, const uint64_t *a, const uint64_t *b, uint64_t *c,
                             int64_t n, const LaunchShape &s, cudaStream_t st) {
   return with_geo(F, [&](auto g) {
-    if (F.phi_tab)
-      k_fused_fast<IVC_OP_ADD, decltype(g), true><<<s.grid, s.block, s.smem, st>>>(F, a, b, c, n,
-                                                                                  0.0f);
+    if (F.phi_tab || decltype(g)::MAP == MAP_TANH)
+      IVC_LAUNCH((k_fused_fast<IVC_OP_ADD, decltype(g), true>), F, a, b, c, n, 0.0f);
     else  // no per-code phi^ table (the allocation-free entry point)
-      k_fused_fast<IVC_OP_ADD, decltype(g), false><<<s.grid, s.block, s.smem, st>>>(F, a, b, c,
-                                                                                   n, 0.0f);
+      IVC_LAUNCH((k_fused_fast<IVC_OP_ADD, decltype(g), false>), F, a, b, c, n, 0.0f);
   });
 }
 
 cudaError_t launch_axpy_fast(const DevFormat &F, float alpha, const uint64_t *x, uint64_t *y,
                              int64_t n, const LaunchShape &s, cudaStream_t st) {
   return with_geo(F, [&](auto g) {
-    k_fused_fast<IVC_OP_AXPY, decltype(g), true><<<s.grid, s.block, s.smem, st>>>(F, x, y, y, n,
-                                                                                 alpha);
+    IVC_LAUNCH((k_fused_fast<IVC_OP_AXPY, decltype(g), true>), F, x, y, y, n, alpha);
   });
 }
 
 cudaError_t launch_compress_fast(const DevFormat &F, const float *xyz, int64_t n, uint64_t *w,
                                  ivc_counts *counts, const LaunchShape &s, cudaStream_t st) {
   return with_geo(F, [&](auto g) {
-    k_compress_fast<decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, xyz, n, w, counts);
+    IVC_LAUNCH((k_compress_fast<decltype(g)>), F, xyz, n, w, counts);
   });
 }
 
 cudaError_t launch_decompress_fast(const DevFormat &F, const uint64_t *w, int64_t n, float *xyz,
                                    const LaunchShape &s, cudaStream_t st) {
   return with_geo(F, [&](auto g) {
-    k_decompress_fast<decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, w, n, xyz);
+    IVC_LAUNCH((k_decompress_fast<decltype(g)>), F, w, n, xyz);
   });
 }
 
@@ -691,8 +717,7 @@ cudaError_t launch_update_fast(const DevFormat &F, float dt, const uint64_t *v, 
                                const float *rho, uint64_t *v_out, uint64_t *m_out, int64_t n,
                                const LaunchShape &s, cudaStream_t st) {
   return with_geo(F, [&](auto g) {
-    k_update_fast<decltype(g)><<<s.grid, s.block, s.smem, st>>>(F, dt, v, f, rho, v_out, m_out,
-                                                               n);
+    IVC_LAUNCH((k_update_fast<decltype(g)>), F, dt, v, f, rho, v_out, m_out, n);
   });
 }
 
@@ -704,6 +729,7 @@ cudaError_t launch_tile_scan(const FieldDesc *fields, int nfields, int tile, int
 
 template <int MAP>
 static const void *kernel_ptr(int kind) {
+  using G = std::conditional_t<MAP == MAP_TANH, fast::GeoTanh, fast::GeoPrimary>;
   switch (kind) {
     case K_COMPRESS: return (const void *)k_compress<MAP>;
     case K_DECOMPRESS: return (const void *)k_decompress<MAP>;
@@ -711,13 +737,13 @@ static const void *kernel_ptr(int kind) {
     case K_AXPY: return (const void *)k_axpy<MAP>;
     case K_UPDATE: return (const void *)k_update<MAP>;
     case K_BATCH_ADD: return (const void *)k_batched<MAP, IVC_OP_ADD>;
-    case K_ADD_FAST: return (const void *)k_fused_fast<IVC_OP_ADD, fast::GeoPrimary, true>;
-    case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY, fast::GeoPrimary, true>;
-    case K_UPDATE_FAST: return (const void *)k_update_fast<fast::GeoPrimary>;
-    case K_BATCH_ADD_FAST: return (const void *)k_batched_fast<IVC_OP_ADD, fast::GeoPrimary>;
-    case K_COMPRESS_FAST: return (const void *)k_compress_fast<fast::GeoPrimary>;
-    case K_DECOMPRESS_FAST: return (const void *)k_decompress_fast<fast::GeoPrimary>;
-    case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY, fast::GeoPrimary>;
+    case K_ADD_FAST: return (const void *)k_fused_fast<IVC_OP_ADD, G, true>;
+    case K_AXPY_FAST: return (const void *)k_fused_fast<IVC_OP_AXPY, G, true>;
+    case K_UPDATE_FAST: return (const void *)k_update_fast<G>;
+    case K_BATCH_ADD_FAST: return (const void *)k_batched_fast<IVC_OP_ADD, G>;
+    case K_COMPRESS_FAST: return (const void *)k_compress_fast<G>;
+    case K_DECOMPRESS_FAST: return (const void *)k_decompress_fast<G>;
+    case K_BATCH_AXPY_FAST: return (const void *)k_batched_fast<IVC_OP_AXPY, G>;
     default: return (const void *)k_batched<MAP, IVC_OP_AXPY>;
   }
 }
@@ -727,7 +753,8 @@ int occupancy(int map, int kind, int block, size_t smem) {
                   : map == MAP_TANH  ? kernel_ptr<MAP_TANH>(kind)
                                      : kernel_ptr<MAP_FRACSPLIT>(kind);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) {
+  if (allow_smem(k, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

@@ -6,6 +6,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_2003_02633_gb300", "csrc", "ivc_fast.cuh")
@@ -109,3 +110,45 @@ def test_bin_scale_constants():
             hf, lf = float.fromhex(h), float.fromhex(l)
             assert hf == float(np.float32(float(v))), (g, h)
             assert lf == float(np.float32(float(v - mpf(hf)))), (g, l)
+
+
+@pytest.mark.parametrize("gamma", [0.05, 0.5, 1.0])
+def test_tanh_node_interpolation(gamma):
+    """The tanh map's fast encoder interpolates the bin coordinate t(a) =
+    n_max (tanh(gamma w(a)) + c) / (2c) quadratically from the nearest node
+    j pi / 1024 (w = a / pi for |theta|, 2 a / pi - 1 for phi): within 1e-4
+    bin of t everywhere, for the largest grids and gamma up to 1; and its
+    slope is at most gamma / tanh(gamma) times the uniform map's, the factor
+    the estimate's error band kEpsTanh allows for."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 80
+    rng = np.random.default_rng(17)
+    c = float(mp.tanh(gamma))
+    for nmax, theta, amax in ((262143, True, np.pi), (131071, False, np.pi / 2)):
+        s = nmax / (2 * c)
+        dw = 1 / np.pi if theta else 2 / np.pi
+
+        def t(a):
+            w = a / mp.pi if theta else 2 * a / mp.pi - 1
+            return s * (mp.tanh(gamma * w) + c)
+
+        worst = 0.0
+        for a in rng.uniform(0, amax, 300):
+            j = round(a * 1024 / np.pi)
+            aj = j * np.pi / 1024
+            w = aj / np.pi if theta else 2 * aj / np.pi - 1
+            th = np.tanh(gamma * w)
+            sech2 = 1 - th * th
+            d1 = s * gamma * dw * sech2
+            d2 = s * gamma ** 2 * dw ** 2 * (-2 * sech2 * th) / 2
+            d = a - aj
+            est = t(mp.mpf(aj)) + d1 * d + d2 * d * d
+            worst = max(worst, float(abs(est - t(mp.mpf(a)))))
+        assert worst < 1e-4, (nmax, gamma, worst)
+        # slope against the uniform map's n_max / (2 pi) (theta) or n_max / pi (phi)
+        uni = nmax / (2 * np.pi) if theta else nmax / np.pi
+        assert s * gamma * dw / uni <= gamma / c + 1e-12
+    assert gamma / c <= 1.32
+    src = open(SRC).read()
+    eps = float(re.search(r"kEpsTanh = ([0-9.]+)f", src).group(1))
+    assert eps >= 1.32 * 0.0045
