@@ -63,7 +63,8 @@ def kernel_source_hash() -> str:
     (the committed DRAM-traffic figure is valid only for that exact code)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2003_02633_gb300", "csrc")
-    files = [os.path.join(csrc, f) for f in ("ivc_device.cuh", "ivc_fast.cuh", "ivc_ops.cu")]
+    files = [os.path.join(csrc, f) for f in ("ivc_internal.h", "ivc_device.cuh", "ivc_exact.cuh",
+                                              "ivc_fast.cuh", "ivc_ops.cu")]
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())

@@ -8,8 +8,10 @@ memory.
 Through the C ABI it must give the words ivc_add gives, on calls in a row
 (the second with a different format, so the shared array is rewritten), also
 when two streams start with the same format at once; it must reject formats
-whose tables do not fit the array; and a call with a format the library has
-never seen must leave the device's free memory unchanged.
+whose tables do not fit the array; under stream capture it must refuse a call
+that would rewrite the array and capture one that would not; and a call with a
+format the library has never seen must leave the device's free memory
+unchanged.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test."""
@@ -101,6 +103,43 @@ def test_noalloc_rejects_oversized_tables():
     st = L.ivc_add_noalloc(ctypes.byref(big), x.data_ptr(), x.data_ptr(), x.data_ptr(), 8, s)
     assert st in (ivc.IVC_ERR_NOMEM, ivc.IVC_ERR_FORMAT)
     torch.cuda.synchronize()
+
+
+def test_noalloc_under_stream_capture():
+    """While a stream captures, a call that would rewrite the array (another
+    format) is refused with IVC_ERR_UNSUPPORTED and enqueues nothing; a call
+    with the format the array holds is captured, and the replayed graph gives
+    ivc_add's words."""
+    fo, fg, wa, wb, pre = _inputs("primary", (1 << 16) + 5, seed=106)
+    _, fg2, _, _, _ = _inputs("L1717", 64, seed=107)
+    out = torch.full_like(wa, -1)
+    ivc.add_noalloc(fg, wa, wb, out)           # the array holds the primary tables
+    torch.cuda.synchronize()
+    want = ivc.add(fg, wa, wb)
+    out.fill_(-1)
+    torch.cuda.synchronize()
+    L = ivc.load()
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    marker = torch.zeros(1, dtype=torch.int64, device=DEV)
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        s = torch.cuda.current_stream().cuda_stream
+        st_other = L.ivc_add_noalloc(ctypes.byref(fg2), wa.data_ptr(), wb.data_ptr(),
+                                     out.data_ptr(), wa.shape[0], s)
+        st_same = L.ivc_add_noalloc(ctypes.byref(fg), wa.data_ptr(), wb.data_ptr(),
+                                    out.data_ptr(), wa.shape[0], s)
+        marker.add_(1)
+        graph.capture_end()
+    torch.cuda.synchronize()
+    assert st_other == ivc.IVC_ERR_UNSUPPORTED
+    assert st_same == ivc.IVC_OK
+    assert int(out[0].item()) == -1            # nothing ran while capturing
+    graph.replay()
+    torch.cuda.synchronize()
+    assert int(marker.item()) == 1
+    check_words(fo, pre, out.cpu().numpy().view(np.uint64), want.cpu().numpy().view(np.uint64),
+                "noalloc replayed from a graph")
 
 
 _FRESH = r"""
