@@ -41,6 +41,14 @@ struct FrBasisDev {
   int q;
   float dm[kMaxQ][kMaxQ];  // dm[i][a] = l_a'(xi_i)
   float lm[kMaxQ], lp[kMaxQ], gl[kMaxQ], gr[kMaxQ];
+  // Index tables, so that the kernels' loops over points and flux points
+  // divide nothing by q.  Flux point f: first solution point of its line
+  // (bits 0-7), the line's point stride (8-15), side (16), axis (17-18).
+  // Solution point k: its indices i, j, l along the three axes (2 bits each,
+  // bits 0-5) and, per axis c, the flux point of side 0 on its line (7 bits
+  // each from bit 6 + 7c).
+  int fdesc[6 * kMaxQ * kMaxQ];
+  int pdesc[kMaxQ * kMaxQ * kMaxQ];
 };
 
 struct FrGasDev {
@@ -228,18 +236,20 @@ struct CodecOf<F32Rows> {
 
 // ------------------------------------------------------------ index helpers
 
-__device__ __forceinline__ void point_ijk(int k, int q, int ijk[3]) {
+// The definitions of the point and flux-point numbering; the host builds the
+// kernels' index tables (FrBasisDev::fdesc, pdesc) from them.
+__host__ __device__ __forceinline__ void point_ijk(int k, int q, int ijk[3]) {
   ijk[0] = k % q;
   ijk[1] = (k / q) % q;
   ijk[2] = k / (q * q);
 }
 
-__device__ __forceinline__ int point_of(const int ijk[3], int q) {
+__host__ __device__ __forceinline__ int point_of(const int ijk[3], int q) {
   return (ijk[2] * q + ijk[1]) * q + ijk[0];
 }
 
 // Flux point f -> face axis c, side s and the indices along the other axes.
-__device__ __forceinline__ void face_of(int f, int q, int &c, int &s, int ijk[3]) {
+__host__ __device__ __forceinline__ void face_of(int f, int q, int &c, int &s, int ijk[3]) {
   const int face = f / (q * q), ab = f % (q * q);
   c = face >> 1;
   s = face & 1;
@@ -250,10 +260,47 @@ __device__ __forceinline__ void face_of(int f, int q, int &c, int &s, int ijk[3]
 }
 
 // Flux point of side s of axis c on the line of solution point ijk.
-__device__ __forceinline__ int flux_point(int c, int s, const int ijk[3], int q) {
+__host__ __device__ __forceinline__ int flux_point(int c, int s, const int ijk[3], int q) {
   const int o0 = c == 0 ? 1 : 0, o1 = c == 2 ? 1 : 2;
   return (2 * c + s) * q * q + ijk[o1] * q + ijk[o0];
 }
+
+// The line of solution points through flux point f, from the table.
+struct FaceLine {
+  int base, stride, side, axis;
+};
+
+__device__ __forceinline__ FaceLine face_line(const FrBasisDev &B, int f) {
+  const int d = B.fdesc[f];
+  return FaceLine{d & 0xff, (d >> 8) & 0xff, (d >> 16) & 1, (d >> 17) & 3};
+}
+
+// Index of solution point k along axis c, and the flux point of side 0 on
+// its line along c, from the table entry pd = B.pdesc[k].
+__device__ __forceinline__ int pd_index(int pd, int c) { return (pd >> (2 * c)) & 3; }
+__device__ __forceinline__ int pd_flux0(int pd, int c) { return (pd >> (6 + 7 * c)) & 0x7f; }
+
+// (tile, sub) = divmod(it, nsub) for it = first, first + step, ... (a
+// per-warp or per-block item loop), advanced without a 64-bit division per
+// item; tile < ntiles exactly while it < ntiles * nsub.
+struct ItemWalk {
+  int64_t tile, dtile;
+  int sub, dsub, nsub;
+  __device__ ItemWalk(int64_t first, int64_t step, int n) : nsub(n) {
+    tile = first / n;
+    sub = (int)(first - tile * n);
+    dtile = step / n;
+    dsub = (int)(step - dtile * n);
+  }
+  __device__ void next() {
+    tile += dtile;
+    sub += dsub;
+    if (sub >= nsub) {
+      sub -= nsub;
+      ++tile;
+    }
+  }
+};
 
 // ------------------------------------------------------------ step 5
 
@@ -284,17 +331,21 @@ __global__ void __launch_bounds__(kThreads) k_fr_grad(const __grid_constant__ De
     }
     __syncthreads();
     for (int k = warp; k < ns; k += kWarps) {
-      int ijk[3];
-      point_ijk(k, q, ijk);
+      const int pd = B.pdesc[k];
       float2 g[3];
+#pragma unroll
       for (int c = 0; c < 3; ++c) {
+        const int ic = pd_index(pd, c);
         const int stride = c == 0 ? 1 : (c == 1 ? q : q * q);
-        const int base = k - ijk[c] * stride;
+        const float *r = sw + (k - ic * stride) * kTile + lane;
         float ga = 0.0f, gb = 0.0f;
-        for (int a = 0; a < q; ++a) {
-          const float d = B.dm[ijk[c]][a];
-          ga = fmaf(d, sw[(base + a * stride) * kTile + lane], ga);
-          gb = fmaf(d, sw[(base + a * stride) * kTile + lane + 32], gb);
+#pragma unroll
+        for (int a = 0; a < kMaxQ; ++a) {
+          if (a < q) {
+            const float d = B.dm[ic][a];
+            ga = fmaf(d, r[a * stride * kTile], ga);
+            gb = fmaf(d, r[a * stride * kTile + 32], gb);
+          }
         }
         g[c] = make_float2(ga, gb);
       }
@@ -343,8 +394,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_correct(const __grid_constant__
     }
     __syncthreads();
     for (int k = warp; k < ns; k += kWarps) {
-      int ijk[3];
-      point_ijk(k, q, ijk);
+      const int pd = B.pdesc[k];
       const int64_t idx = ((int64_t)k * nv + v) * ld;
       typename C::Raw nxt = cur;
       if (k + kWarps < ns) {
@@ -354,9 +404,10 @@ __global__ void __launch_bounds__(kThreads) k_fr_correct(const __grid_constant__
       float2 g[3];
       codec.decode_raw(cur, g[0], g[1], g[2]);
       cur = nxt;
+#pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int fl = flux_point(c, 0, ijk, q), fr = fl + q * q;
-        const float wl = B.gl[ijk[c]], wr = B.gr[ijk[c]];
+        const int fl = pd_flux0(pd, c), fr = fl + q * q;
+        const float wl = B.gl[pd_index(pd, c)], wr = B.gr[pd_index(pd, c)];
         g[c].x = fmaf(wr, sd[fr * kTile + lane], fmaf(wl, sd[fl * kTile + lane], g[c].x));
         g[c].y = fmaf(wr, sd[fr * kTile + lane + 32],
                       fmaf(wl, sd[fl * kTile + lane + 32], g[c].y));
@@ -424,21 +475,20 @@ __device__ __forceinline__ void stage_rows(const C &codec, const typename C::T *
   }
 }
 
-// Value at flux point f of component c of the staged rows (q-term sum along
-// the face's axis), for tile elements lane and lane + 32.
-__device__ __forceinline__ float2 line_value(const float *sx, const FrBasisDev &B, int f, int comp,
-                                             int lane) {
-  const int q = B.q;
-  int c, s, ijk[3];
-  face_of(f, q, c, s, ijk);
-  const int stride = c == 0 ? 1 : (c == 1 ? q : q * q);
-  const int base = point_of(ijk, q);
+// Value on face line fl of component comp of the staged rows (q-term sum
+// along the face's axis), for tile elements lane and lane + 32.
+__device__ __forceinline__ float2 line_value(const float *sx, const FrBasisDev &B,
+                                             const FaceLine &fl, int comp, int lane) {
+  const float *r = sx + (fl.base * 3 + comp) * kTile + lane;
+  const int step = fl.stride * 3 * kTile;
   float a = 0.0f, b = 0.0f;
-  for (int i = 0; i < q; ++i) {
-    const float l = s ? B.lp[i] : B.lm[i];
-    const float *r = sx + ((base + i * stride) * 3 + comp) * kTile;
-    a = fmaf(l, r[lane], a);
-    b = fmaf(l, r[lane + 32], b);
+#pragma unroll
+  for (int i = 0; i < kMaxQ; ++i) {
+    if (i < B.q) {
+      const float l = fl.side ? B.lp[i] : B.lm[i];
+      a = fmaf(l, r[i * step], a);
+      b = fmaf(l, r[i * step + 32], b);
+    }
   }
   return make_float2(a, b);
 }
@@ -466,9 +516,10 @@ __global__ void __launch_bounds__(kThreads) k_fr_interp(const __grid_constant__ 
     stage_rows<C::kWords>(codec, X, sx, ns, nv, v, ld, e0, ne, cs_in);
     __syncthreads();
     for (int f = warp; f < nf; f += kWarps) {
-      const float2 x = line_value(sx, B, f, 0, lane);
-      const float2 y = line_value(sx, B, f, 1, lane);
-      const float2 z = line_value(sx, B, f, 2, lane);
+      const FaceLine fl = face_line(B, f);
+      const float2 x = line_value(sx, B, fl, 0, lane);
+      const float2 y = line_value(sx, B, fl, 1, lane);
+      const float2 z = line_value(sx, B, fl, 2, lane);
       const int64_t idx = ((int64_t)f * nv + v) * ld;
       codec.store2(Xf, idx + ea, idx + eb, va, vb, cs_out, x, y, z);
     }
@@ -514,9 +565,9 @@ __global__ void __launch_bounds__(kThreads) k_fr_fcorr(const __grid_constant__ D
     __syncthreads();
     for (int f = warp; f < nf; f += kWarps) {
       const float2 nfn = nf_at(f + kWarps);
-      const int face = f / (q * q);
-      const float2 t = line_value(sx, B, f, face >> 1, lane);
-      const float sg = (face & 1) ? 1.0f : -1.0f;
+      const FaceLine fl = face_line(B, f);
+      const float2 t = line_value(sx, B, fl, fl.axis, lane);
+      const float sg = fl.side ? 1.0f : -1.0f;
       const int64_t idx = ((int64_t)f * nv + v) * ld;
       if (va) Fc[idx + ea] = fmaf(-sg, t.x, nfc.x);
       if (vb) Fc[idx + eb] = fmaf(-sg, t.y, nfc.y);
@@ -632,12 +683,11 @@ __global__ void __launch_bounds__(kThreads) k_fr_flux(const __grid_constant__ De
   C codec = CodecOf<C>::make(F, smem, L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ntiles = (ne + kTile - 1) / kTile;
-  const int64_t items = ntiles * ns;                        // (tile, point) per warp
   const int64_t cs5 = (int64_t)ns * 5 * ld, cs3 = (int64_t)ns * 3 * ld;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
-  for (int64_t it = gw; it < items; it += nw) {
-    const int64_t e0 = (it / ns) * kTile;
-    const int k = (int)(it % ns);
+  for (ItemWalk iw(gw, nw, ns); iw.tile < ntiles; iw.next()) {
+    const int64_t e0 = iw.tile * kTile;
+    const int k = iw.sub;
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
     PointIn<C> in;
@@ -666,13 +716,26 @@ __global__ void __launch_bounds__(kThreads) k_fr_flux(const __grid_constant__ De
 }
 
 // The element across face (c, s) of element e on a periodic Ex x Ey x Ez
-// mesh, e = (ez Ey + ey) Ex + ex.
+// mesh, e = (ez Ey + ey) Ex + ex.  Two 32-bit divisions where the mesh has
+// fewer than 2^32 elements (always, in practice), 64-bit ones otherwise.
 __device__ __forceinline__ int64_t neighbour(int64_t e, int c, int s, int Ex, int Ey, int Ez) {
-  int64_t ix = e % Ex, iy = (e / Ex) % Ey, iz = e / ((int64_t)Ex * Ey);
+  int64_t ix, iy, iz;
+  const int64_t exy = (int64_t)Ex * Ey;
+  if (exy * Ez <= (int64_t)0xffffffffu) {
+    const uint32_t u = (uint32_t)e, uxy = (uint32_t)exy;
+    const uint32_t z = u / uxy, r = u - z * uxy, y = r / (uint32_t)Ex;
+    ix = r - y * (uint32_t)Ex;
+    iy = y;
+    iz = z;
+  } else {
+    ix = e % Ex;
+    iy = (e / Ex) % Ey;
+    iz = e / exy;
+  }
   const int d = s ? 1 : -1;
-  if (c == 0) ix = (ix + d + Ex) % Ex;
-  else if (c == 1) iy = (iy + d + Ey) % Ey;
-  else iz = (iz + d + Ez) % Ez;
+  if (c == 0) ix = ix + d == Ex ? 0 : (ix + d < 0 ? Ex - 1 : ix + d);
+  else if (c == 1) iy = iy + d == Ey ? 0 : (iy + d < 0 ? Ey - 1 : iy + d);
+  else iz = iz + d == Ez ? 0 : (iz + d < 0 ? Ez - 1 : iz + d);
   return (iz * Ey + iy) * Ex + ix;
 }
 
@@ -717,14 +780,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_fr_commonvis(
   const int nf = 6 * q * q, nplus = 3 * q * q;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ntiles = (ne + kTile - 1) / kTile;
-  const int64_t items = ntiles * nplus;
   const int64_t cs5 = (int64_t)nf * 5 * ld, cs3 = (int64_t)nf * 3 * ld, cs1 = (int64_t)nf * ld;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
-  for (int64_t it = gw; it < items; it += nw) {
-    const int64_t e0 = (it / nplus) * kTile;
-    const int j = (int)(it % nplus);                // + face point: axis c, in-face index
-    const int c = j / (q * q);
-    const int f = (2 * c + 1) * q * q + j % (q * q), fo = f - q * q;
+  const int qq = q * q;
+  for (ItemWalk iw(gw, nw, nplus); iw.tile < ntiles; iw.next()) {
+    const int64_t e0 = iw.tile * kTile;
+    const int j = iw.sub;                           // + face point: axis c, in-face index
+    const int c = (j >= qq) + (j >= 2 * qq);
+    const int f = (2 * c + 1) * qq + (j - c * qq), fo = f - qq;
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
     const int64_t pa = va ? neighbour(ea, c, 1, Ex, Ey, Ez) : 0;
@@ -927,11 +990,10 @@ __global__ void __launch_bounds__(kThreads) k_fr_flux_w(const __grid_constant__ 
   float2 *sc = reinterpret_cast<float2 *>(smem + L.off_stage) + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ntiles = (ne + kTile - 1) / kTile;
-  const int64_t items = ntiles * ns;                        // (tile, point) per warp
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
-  for (int64_t it = gw; it < items; it += nw) {
-    const int64_t e0 = (it / ns) * kTile;
-    const int k = (int)(it % ns);
+  for (ItemWalk iw(gw, nw, ns); iw.tile < ntiles; iw.next()) {
+    const int64_t e0 = iw.tile * kTile;
+    const int k = iw.sub;
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
     fetch_rows_async(sc, 8, G, S, k, ea, eb, va, vb, ld);
@@ -969,13 +1031,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_commonvis_w(
   const int nplus = 3 * q * q;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ntiles = (ne + kTile - 1) / kTile;
-  const int64_t items = ntiles * nplus;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
-  for (int64_t it = gw; it < items; it += nw) {
-    const int64_t e0 = (it / nplus) * kTile;
-    const int j = (int)(it % nplus);                // + face point: axis c, in-face index
-    const int c = j / (q * q);
-    const int f = (2 * c + 1) * q * q + j % (q * q), fo = f - q * q;
+  const int qq = q * q;
+  for (ItemWalk iw(gw, nw, nplus); iw.tile < ntiles; iw.next()) {
+    const int64_t e0 = iw.tile * kTile;
+    const int j = iw.sub;                           // + face point: axis c, in-face index
+    const int c = (j >= qq) + (j >= 2 * qq);
+    const int f = (2 * c + 1) * qq + (j - c * qq), fo = f - qq;
     const int64_t ea = e0 + lane, eb = e0 + lane + 32;
     const bool va = ea < ne, vb = eb < ne;
     const int64_t pa = va ? neighbour(ea, c, 1, Ex, Ey, Ez) : 0;
@@ -1094,6 +1156,20 @@ FrBasisDev basis_dev(const ivc_fr_basis &b) {
     B.lp[i] = b.lp[i];
     B.gl[i] = b.gl[i];
     B.gr[i] = b.gr[i];
+  }
+  const int q = B.q;
+  for (int f = 0; f < 6 * q * q; ++f) {
+    int c, s, ijk[3];
+    face_of(f, q, c, s, ijk);
+    const int stride = c == 0 ? 1 : (c == 1 ? q : q * q);
+    B.fdesc[f] = point_of(ijk, q) | (stride << 8) | (s << 16) | (c << 17);
+  }
+  for (int k = 0; k < q * q * q; ++k) {
+    int ijk[3];
+    point_ijk(k, q, ijk);
+    int d = ijk[0] | (ijk[1] << 2) | (ijk[2] << 4);
+    for (int c = 0; c < 3; ++c) d |= flux_point(c, 0, ijk, q) << (6 + 7 * c);
+    B.pdesc[k] = d;
   }
   return B;
 }
