@@ -41,6 +41,7 @@ constexpr int kCoreBytes = 128;      // one 8-row x 16-byte core matrix
 constexpr int kAStep = (kTM / 8) * 2 * kCoreBytes;       // bytes of A per K step
 constexpr int kABuf = kKStepsC * kAStep;                 // one A buffer (head or tail)
 constexpr long long kWaitCycles = 2000000000ll;
+constexpr uint32_t kSuspendNs = 65536;
 constexpr int kMaxNs = 64;
 constexpr int kMaxNv = 5;
 
@@ -100,17 +101,20 @@ __device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count) {
                : "memory");
 }
 
-// Bounded wait for the completion of the phase with the given parity.
+// Bounded wait for the completion of the phase with the given parity.  Each
+// try_wait may suspend the thread for up to kSuspendNs until the phase
+// completes, instead of returning at once, so a waiting warp issues few
+// instructions.
 __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (ok) return true;
     if (clock64() - t0 > kWaitCycles) return false;
@@ -367,8 +371,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         } else {
           float2 X, Y, Z;
           if (MODE == TC_FAST) {
-            fast::decode2_near<fast::GeoPrimary>(cur.w0[v], cur.w1[v], F, tab_t, tab_p, X, Y,
-                                                 Z);
+            fast::decode2_f32<fast::GeoPrimary>(cur.w0[v], cur.w1[v], F, tab_t, tab_p, X, Y,
+                                                Z);
           } else {
             const float3 a0 = decode_word<MAP>(cur.w0[v], F, tab_t, tab_p);
             const float3 a1 = decode_word<MAP>(cur.w1[v], F, tab_t, tab_p);
