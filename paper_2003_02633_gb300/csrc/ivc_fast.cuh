@@ -26,6 +26,13 @@ constexpr float kEps = 0.005f;      // bin-coordinate estimate error bound (with
 // the tanh map's estimate: the atan error scaled by the map's largest slope
 // relative to the uniform map, gamma / tanh(gamma) <= 1.32 for gamma <= 1
 constexpr float kEpsTanh = 0.0065f;
+// Bin-coordinate shift between the direction of a vector v and that of
+// RN(rho v) for a positive rho: each component moves by at most 2^-24
+// relative (or, below the FP32 normal range, by an absolute amount far below
+// 2^-24 |v| inside the fast window), which turns theta = atan2(y, x) and
+// phi = atan2(|(x, y)|, z) by at most 2^-24 rad: n_max / (2 pi) 2^-24 or
+// n_max / pi 2^-24 < 0.0025 bin, times at most 1.32 for the tanh map.
+constexpr float kReuseEps = 0.004f;
 
 // The layouts this path serves: grid sizes n_theta_max = N, n_phi_max = M,
 // head-table steps 2^ST (theta grid pi m / N) and 2^SP (phi grid
@@ -720,11 +727,18 @@ struct Enc2 {
 // Encodes two vectors.  The word of a vector with a pending exact decision,
 // or outside the fast path's magnitude window (zero, tiny, huge, Inf, NaN:
 // the generic encoder, with its range handling and events), is provisional:
-// the caller queues it with push2.
-template <class G>
+// the caller queues it with push2.  est (optional) receives the angle
+// estimates.  REUSE: the vectors are positive multiples RN(rho v) of vectors
+// v whose estimates est holds; those stand for the angle estimates here,
+// with the ambiguity band widened by kReuseEps, and an element with force set
+// (rho not positive and finite, or v outside the window) goes to the generic
+// encoder.
+template <class G, bool REUSE = false>
 __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevFormat &F,
                                         const TabEntry *__restrict__ tab_t,
-                                        const TabEntry *__restrict__ tab_p) {
+                                        const TabEntry *__restrict__ tab_p,
+                                        Est2 *est = nullptr, bool force0 = false,
+                                        bool force1 = false) {
   constexpr int kN = G::N, kM = G::M;
   Enc2 r;
   // squares and sums in float-float
@@ -759,9 +773,16 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   // a magnitude within the norm's error bound of an FP32 rounding boundary
   // (about 2^-18 of the vectors) is settled by the generic encoder, through
   // the queue like the out-of-window vectors
-  const bool gq0 = gen0 || nslow0, gq1 = gen1 || nslow1;
+  const bool gq0 = gen0 || nslow0 || (REUSE && force0);
+  const bool gq1 = gen1 || nslow1 || (REUSE && force1);
   // angle estimates
-  const Est2 e = estimate2<G>(x, y, z, r2h, r2l, tab_t, tab_p);
+  Est2 e;
+  if constexpr (REUSE) {
+    e = *est;
+  } else {
+    e = estimate2<G>(x, y, z, r2h, r2l, tab_t, tab_p);
+    if (est) *est = e;
+  }
   // k = floor(t) clamped to [0, n_max - 1]; the fraction absorbs the clamp
   // (t = n_max gives fraction 1, t < 0 a negative one: never flagged)
   float2 ft = add2(e.fl_t, bc((float)((kN - 1) / 2)));
@@ -779,7 +800,7 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
   int np0 = kp0 + (frp.x >= 0.5f ? 1 : 0), np1 = kp1 + (frp.y >= 0.5f ? 1 : 0);
   // pending exact decisions: kinds within kEps of a rounding boundary
   // (bit 0 theta, bit 1 phi); their words are provisional
-  constexpr float eps = G::MAP == MAP_TANH ? kEpsTanh : kEps;
+  constexpr float eps = (G::MAP == MAP_TANH ? kEpsTanh : kEps) + (REUSE ? kReuseEps : 0.0f);
   r.pend0 = gq0 ? 4u : (fabsf(frt.x - 0.5f) <= eps ? 1u : 0u) | (fabsf(frp.x - 0.5f) <= eps ? 2u : 0u);
   r.pend1 = gq1 ? 4u : (fabsf(frt.y - 0.5f) <= eps ? 1u : 0u) | (fabsf(frp.y - 0.5f) <= eps ? 2u : 0u);
   r.nt0 = (r.pend0 & 1u) ? kt0 : nt0;

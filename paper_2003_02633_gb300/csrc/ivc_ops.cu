@@ -398,14 +398,19 @@ __global__ void __launch_bounds__(256, 3) k_update_fast(const __grid_constant__ 
     const float2 sx = fast::fma2(fast::bc(dt), gx, ux);
     const float2 sy = fast::fma2(fast::bc(dt), gy, uy);
     const float2 sz = fast::fma2(fast::bc(dt), gz, uz);
-    const fast::Enc2 e = fast::encode2<G>(sx, sy, sz, F, tab_t, tab_p);
+    fast::Est2 est;
+    const fast::Enc2 e = fast::encode2<G>(sx, sy, sz, F, tab_t, tab_p, &est);
     if (act) __stcs(o2 + i, make_ulonglong2(e.w0, e.w1));
     fast::push2<G>(wq, act, e, sx, sy, sz, v_out + 2 * i, F, tab_t, tab_p);
     if (want_m) {
       const float2 q = act ? make_float2(__ldcs(rho + 2 * i), __ldcs(rho + 2 * i + 1))
                            : make_float2(0.0f, 0.0f);
       const float2 mx = fast::mul2(q, sx), my = fast::mul2(q, sy), mz = fast::mul2(q, sz);
-      const fast::Enc2 em = fast::encode2<G>(mx, my, mz, F, tab_t, tab_p);
+      // m = RN(rho v) points where v does (rho > 0): v's angle estimates
+      // serve m, with the ambiguity band widened by the rounding of rho v
+      const bool f0 = !(q.x > 0.0f && q.x < INFINITY) || (e.pend0 & 4u) != 0u;
+      const bool f1 = !(q.y > 0.0f && q.y < INFINITY) || (e.pend1 & 4u) != 0u;
+      const fast::Enc2 em = fast::encode2<G, true>(mx, my, mz, F, tab_t, tab_p, &est, f0, f1);
       if (act) __stcs(m2 + i, make_ulonglong2(em.w0, em.w1));
       fast::push2<G>(wq, act, em, mx, my, mz, m_out + 2 * i, F, tab_t, tab_p);
     }

@@ -121,6 +121,34 @@ def test_pointwise_update_tgv():
     check_words(fo, rho[:, None] * pre, _host_words(mg), mo, "update m")
 
 
+def test_pointwise_update_momentum_any_rho():
+    """m = encode(rho * v_new): the fast kernel takes m's angle estimates from
+    v_new's (m points where v_new does when rho > 0), with a wider ambiguity
+    band, and sends m to the generic encoder when rho is not positive and
+    finite or v_new lies outside the fast window.  Random directions and
+    magnitudes, edge vectors, and densities from 10^U(-3, 3) mixed with 0,
+    -0, negative, tiny, huge, Inf and NaN values, against the oracle."""
+    fo, fg = formats("primary")
+    v, f = synth.roundtrip_inputs((1 << 18) + 5, seed=61)
+    rng = np.random.default_rng(62)
+    rho = (10.0 ** rng.uniform(-3, 3, v.shape[0])).astype(np.float32)
+    special = np.float32([0.0, -0.0, -1.0, -2.5e3, 1e-38, 3e38, np.inf, -np.inf, np.nan, 1e-45])
+    idx = rng.choice(v.shape[0], 4000, replace=False)
+    rho[idx] = special[rng.integers(0, len(special), len(idx))]
+    with np.errstate(invalid="ignore", over="ignore"):
+        wv, wf = O.compress(fo, v), O.compress(fo, f)
+        dt = np.float32(1e-3)
+        vo, mo = O.update(fo, dt, wv, wf, rho, want_m=True)
+        dv = O.decompress(fo, wv).astype(np.float64)
+        df = O.decompress(fo, wf).astype(np.float64)
+        pre = (np.float64(dt) * df + dv).astype(np.float32)
+        pre_m = (rho[:, None].astype(np.float64) * pre).astype(np.float32)
+    vg, mg = ivc.pointwise_update(fg, dt, _words_dev(wv), _words_dev(wf), rho=_dev(rho),
+                                  m_out=torch.empty(len(wv), dtype=torch.int64, device=DEV))
+    check_words(fo, pre, _host_words(vg), vo, "update v")
+    check_words(fo, pre_m, _host_words(mg), mo, "update m, any rho")
+
+
 def test_soa_layout(c0):
     fo, fg = formats("primary")
     x = c0[0][:70001]
