@@ -825,7 +825,7 @@ __device__ __forceinline__ Enc2 encode2(float2 x, float2 y, float2 z, const DevF
 // final word overwrites the provisional one (same warp, ordered by
 // __syncwarp).  Capacity: at most 31 items wait between pushes and one push
 // adds at most 64.
-constexpr int kQueueCap = 96;
+constexpr int kQueueCap = 95;
 
 struct PendItem {
   uint64_t *dst;   // word to overwrite
