@@ -374,11 +374,20 @@ __device__ __forceinline__ void phi_pair(uint32_t np0, uint32_t np1, const DevFo
 
 // Decodes two words; returns false in *ok for an element that needs the
 // generic path (non-finite word or an ambiguous rounding).
+// The tanh map's per-code table entries of a word pair, staged in shared
+// memory by stage_entries (slot stride ss float4): theta^ of w0, of w1, phi^
+// of w0, of w1.
+struct Staged {
+  const float4 *p;
+  int ss;
+};
+
 template <class G, bool PT>
 __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const DevFormat &F,
                                         const TabEntry *__restrict__ tab_t,
                                         const TabEntry *__restrict__ tab_p, float2 &X,
-                                        float2 &Y, float2 &Z, bool &slow0, bool &slow1) {
+                                        float2 &Y, float2 &Z, bool &slow0, bool &slow1,
+                                        const Staged *stg = nullptr) {
   const uint32_t hi0 = (uint32_t)(w0 >> 32), lo0 = (uint32_t)w0;
   const uint32_t hi1 = (uint32_t)(w1 >> 32), lo1 = (uint32_t)w1;
   const uint32_t E0 = G::efield(hi0), E1 = G::efield(hi1);
@@ -397,8 +406,10 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const DevForma
     // signed float-float cos/sin of every code's angle, read through L2
     const float4 *dt = reinterpret_cast<const float4 *>(F.dec_t);
     const float4 *dp = reinterpret_cast<const float4 *>(F.dec_p);
-    const float4 a0 = __ldg(dt + nt0), a1 = __ldg(dt + nt1);
-    const float4 b0 = __ldg(dp + np0), b1 = __ldg(dp + np1);
+    const float4 a0 = stg ? stg->p[0] : __ldg(dt + nt0);
+    const float4 a1 = stg ? stg->p[stg->ss] : __ldg(dt + nt1);
+    const float4 b0 = stg ? stg->p[2 * stg->ss] : __ldg(dp + np0);
+    const float4 b1 = stg ? stg->p[3 * stg->ss] : __ldg(dp + np1);
     ct = abs_ff2(make_float2(a0.x, a1.x), make_float2(a0.y, a1.y), sgx);
     st = abs_ff2(make_float2(a0.z, a1.z), make_float2(a0.w, a1.w), sgy);
     cp = abs_ff2(make_float2(b0.x, b1.x), make_float2(b0.y, b1.y), sgz);
@@ -929,14 +940,39 @@ __device__ __forceinline__ void drain(WarpQueue &wq, const DevFormat &F, const T
   __syncwarp();
 }
 
+// 16-byte asynchronous global-to-shared copy (L2 only).
+__device__ __forceinline__ void cp_async16(float4 *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+
+// Starts the copies of the tanh map's per-code table entries of a word pair
+// into the shared-memory slots dst[0], dst[ss], dst[2 ss], dst[3 ss] (any
+// field values index inside the tables: n_theta <= N, n_phi <= M).
+template <class G>
+__device__ __forceinline__ void stage_entries(uint64_t w0, uint64_t w1, const DevFormat &F,
+                                              float4 *dst, int ss) {
+  uint32_t nt0, np0, nt1, np1;
+  G::unpack((uint32_t)(w0 >> 32), (uint32_t)w0, nt0, np0);
+  G::unpack((uint32_t)(w1 >> 32), (uint32_t)w1, nt1, np1);
+  cp_async16(dst, F.dec_t + nt0);
+  cp_async16(dst + ss, F.dec_t + nt1);
+  cp_async16(dst + 2 * ss, F.dec_p + np0);
+  cp_async16(dst + 3 * ss, F.dec_p + np1);
+}
+
 // Decodes two words through the fast path, falling back per element.  PT:
-// F.phi_tab holds the per-code phi^ table.
+// F.phi_tab holds the per-code phi^ table.  stg: the tanh map's entries,
+// staged.
 template <class G, bool PT = true>
 __device__ __forceinline__ void decode2_full(uint64_t w0, uint64_t w1, const DevFormat &F,
                                              const TabEntry *tab_t, const TabEntry *tab_p,
-                                             float2 &X, float2 &Y, float2 &Z) {
+                                             float2 &X, float2 &Y, float2 &Z,
+                                             const Staged *stg = nullptr) {
   bool s0, s1;
-  decode2<G, PT>(w0, w1, F, tab_t, tab_p, X, Y, Z, s0, s1);
+  decode2<G, PT>(w0, w1, F, tab_t, tab_p, X, Y, Z, s0, s1, stg);
   if (s0) {
     const float3 v = decode_generic<G::MAP>(w0, F, tab_t, tab_p);
     X.x = v.x; Y.x = v.y; Z.x = v.z;

@@ -215,18 +215,77 @@ __global__ void __launch_bounds__(256) k_update(const __grid_constant__ DevForma
 // calling threads: warp `warp` of `nwarps` takes word pairs warp*32 + lane,
 // (warp + nwarps)*32 + lane, ...; the trip count is uniform per warp.  The odd
 // tail element goes to the thread with warp == 0 and lane == 0.  PT: the
-// format carries the per-code phi^ table (F.phi_tab).
-template <int OP, class G, bool PT = true>
+// format carries the per-code phi^ table (F.phi_tab).  STG (tanh map): the
+// two per-code table entries of every decoded word are copied into shared
+// memory by cp.async one iteration ahead (`stage`: two buffers of 8 16-byte
+// slots per thread), so that the decode does not wait on its L2 gathers.
+template <int OP, class G, bool PT = true, bool STG = false>
 __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64_t *b, uint64_t *c,
                                                  int64_t n, int64_t warp, int64_t nwarps, int lane,
                                                  float alpha, const DevFormat &F,
                                                  const TabEntry *tab_t, const TabEntry *tab_p,
-                                                 void *qbase) {
+                                                 void *qbase, void *stage = nullptr) {
   fast::WarpQueue wq = fast::warp_queue(qbase);
   const int64_t n2 = n >> 1;
   const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(a);
   const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(b);
   ulonglong2 *c2 = reinterpret_cast<ulonglong2 *>(c);
+  if constexpr (STG) {
+    // words two iterations ahead; slots of a's pair 0-3, b's pair 4-7
+    float4 *sbuf = reinterpret_cast<float4 *>(stage);
+    const int ss = blockDim.x, t = threadIdx.x;
+    const int64_t st = nwarps * 32;
+    ulonglong2 ca = make_ulonglong2(0ull, 0ull), cb = ca, na = ca, nb = ca;
+    if (warp * 32 + lane < n2) {
+      ca = __ldcs(a2 + warp * 32 + lane);
+      cb = __ldcs(b2 + warp * 32 + lane);
+    }
+    if (warp * 32 + lane + st < n2) {
+      na = __ldcs(a2 + warp * 32 + lane + st);
+      nb = __ldcs(b2 + warp * 32 + lane + st);
+    }
+    fast::stage_entries<G>(ca.x, ca.y, F, sbuf + t, ss);
+    fast::stage_entries<G>(cb.x, cb.y, F, sbuf + 4 * ss + t, ss);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    int buf = 0;
+    for (int64_t base = warp * 32; base < n2; base += st) {
+      const int64_t i = base + lane;
+      const bool act = i < n2;
+      const ulonglong2 wa = ca, wb = cb;
+      ca = na;
+      cb = nb;
+      if (i + 2 * st < n2) {
+        na = __ldcs(a2 + i + 2 * st);
+        nb = __ldcs(b2 + i + 2 * st);
+      }
+      // the next iteration's entries into the other buffer (its previous
+      // contents were read by this thread's last iteration), then wait for
+      // this iteration's
+      float4 *nxt = sbuf + (buf ^ 1) * 8 * ss + t;
+      fast::stage_entries<G>(ca.x, ca.y, F, nxt, ss);
+      fast::stage_entries<G>(cb.x, cb.y, F, nxt + 4 * ss, ss);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      const fast::Staged sa{sbuf + buf * 8 * ss + t, ss};
+      const fast::Staged sb{sbuf + buf * 8 * ss + 4 * ss + t, ss};
+      buf ^= 1;
+      float2 ux, uy, uz, vx, vy, vz;
+      fast::decode2_full<G, PT>(wa.x, wa.y, F, tab_t, tab_p, ux, uy, uz, &sa);
+      fast::decode2_full<G, PT>(wb.x, wb.y, F, tab_t, tab_p, vx, vy, vz, &sb);
+      float2 sx, sy, sz;
+      if (OP == IVC_OP_ADD) {
+        sx = fast::add2(ux, vx); sy = fast::add2(uy, vy); sz = fast::add2(uz, vz);
+      } else {
+        sx = fast::fma2(fast::bc(alpha), ux, vx);
+        sy = fast::fma2(fast::bc(alpha), uy, vy);
+        sz = fast::fma2(fast::bc(alpha), uz, vz);
+      }
+      const fast::Enc2 e = fast::encode2<G>(sx, sy, sz, F, tab_t, tab_p);
+      if (act) __stcs(c2 + i, make_ulonglong2(e.w0, e.w1));
+      fast::push2<G>(wq, act, e, sx, sy, sz, c + 2 * i, F, tab_t, tab_p);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else {
   // the next iteration's words are loaded before this iteration's arithmetic
   ulonglong2 na = make_ulonglong2(0ull, 0ull), nb = na;
   if (warp * 32 + lane < n2) {
@@ -256,6 +315,7 @@ __device__ __forceinline__ void fused_fast_range(const uint64_t *a, const uint64
     if (act) __stcs(c2 + i, make_ulonglong2(e.w0, e.w1));
     fast::push2<G>(wq, act, e, sx, sy, sz, c + 2 * i, F, tab_t, tab_p);
   }
+  }
   fast::drain<G>(wq, F, tab_t, tab_p);
   if ((n & 1) && warp == 0 && lane == 0) {
     uint32_t flags = 0;
@@ -275,9 +335,12 @@ __global__ void __launch_bounds__(256, 2) k_fused_fast(const __grid_constant__ D
                                                     const uint64_t *a, const uint64_t *b,
                                                     uint64_t *c, int64_t n, float alpha) {
   IVC_FAST_TABLES(F, G);
-  fused_fast_range<OP, G, PT>(a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                       ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t,
-                       tab_p, IVC_FAST_QUEUE(F, G));
+  constexpr bool kStg = G::MAP == MAP_TANH;
+  fused_fast_range<OP, G, PT, kStg>(
+      a, b, c, n, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+      ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31, alpha, F, tab_t, tab_p,
+      IVC_FAST_QUEUE(F, G),
+      (char *)IVC_FAST_QUEUE(F, G) + (blockDim.x >> 5) * fast::kQueueCap * sizeof(fast::PendItem));
 }
 
 // Compress n AoS vectors (primary layout), two per thread; counts as in
@@ -560,7 +623,11 @@ size_t kernel_smem_bytes(const DevFormat &F, int map, int kind, int block) {
   const size_t tabs = (fastk && map == MAP_TANH)
                           ? (size_t)(F.nest_t + F.nest_p) * sizeof(TabEntry)
                           : table_smem_bytes(F, map);
-  return tabs + (queue ? (size_t)(block / 32) * fast::kQueueCap * sizeof(fast::PendItem) : 0);
+  // the tanh map's fused add / axpy stage their decoder's table entries (two
+  // buffers of 8 16-byte slots per thread)
+  const bool staged = (kind == K_ADD_FAST || kind == K_AXPY_FAST) && map == MAP_TANH;
+  return tabs + (queue ? (size_t)(block / 32) * fast::kQueueCap * sizeof(fast::PendItem) : 0) +
+         (staged ? (size_t)block * 16 * 16 : 0);
 }
 
 #define IVC_DISPATCH_MAP(map, KERNEL, ...)                                                    \

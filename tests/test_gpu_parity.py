@@ -186,6 +186,27 @@ def test_formats(name):
     check_words(fo, pre, got, O.add(fo, wa, wb), f"{name} add")
 
 
+def test_tanh_add_axpy_many_iterations():
+    """The tanh map's fused add and axpy copy every decoded word's two table
+    entries into shared memory one iteration ahead (cp.async, two buffers):
+    2^21 + 3 vectors give each warp about a dozen iterations (both buffers
+    reused several times, odd tail), against the oracle; axpy in place."""
+    fo, fg = formats("tanh")
+    a, b = synth.roundtrip_inputs((1 << 21) + 3, seed=71)
+    wa, wb = O.compress(fo, a), O.compress(fo, b)
+    with np.errstate(invalid="ignore", over="ignore"):
+        da, db = O.decompress(fo, wa), O.decompress(fo, wb)
+        pre = da + db
+        alpha = np.float32(0.7)
+        pre_axpy = (np.float64(alpha) * da.astype(np.float64) + db).astype(np.float32)
+    got = _host_words(ivc.add(fg, _words_dev(wa), _words_dev(wb)))
+    check_words(fo, pre, got, O.add(fo, wa, wb), "tanh add, many iterations")
+    y = _words_dev(wb)
+    ivc.axpy(fg, alpha, _words_dev(wa), y)
+    check_words(fo, pre_axpy, _host_words(y), O.axpy(fo, alpha, wa, wb),
+                "tanh axpy in place, many iterations")
+
+
 def test_counts_match_oracle():
     fo, fg = formats("primary")
     x = synth.precision_vectors(1 << 16, seed=11)
