@@ -419,7 +419,18 @@ __device__ __forceinline__ void decode2(uint64_t w0, uint64_t w1, const DevForma
     // phi^ first: with the per-code table its loads are in flight while
     // theta^ is evaluated
     bool pneg0, pneg1;
-    phi_pair<G, PT>(np0, np1, F, tab_p, cp, sp, pneg0, pneg1);
+    if (stg) {
+      // the per-code phi^ entries, staged (slots 2 and 3)
+      const float4 e0 = stg->p[2 * stg->ss], e1 = stg->p[3 * stg->ss];
+      pneg0 = (int)np0 > G::M - (int)np0;
+      pneg1 = (int)np1 > G::M - (int)np1;
+      cp.h = make_float2(e0.x, e1.x);
+      cp.l = make_float2(e0.y, e1.y);
+      sp.h = make_float2(e0.z, e1.z);
+      sp.l = make_float2(e0.w, e1.w);
+    } else {
+      phi_pair<G, PT>(np0, np1, F, tab_p, cp, sp, pneg0, pneg1);
+    }
     const float2 ntf = add2(make_float2(__uint_as_float(nt0 | 0x4B000000u),
                                         __uint_as_float(nt1 | 0x4B000000u)),
                             bc(-8388608.0f));
@@ -961,6 +972,16 @@ __device__ __forceinline__ void stage_entries(uint64_t w0, uint64_t w1, const De
   cp_async16(dst + ss, F.dec_t + nt1);
   cp_async16(dst + 2 * ss, F.dec_p + np0);
   cp_async16(dst + 3 * ss, F.dec_p + np1);
+}
+// The per-code phi^ entries of a word pair into slots 2 ss and 3 ss.
+template <class G>
+__device__ __forceinline__ void stage_phi(uint64_t w0, uint64_t w1, const DevFormat &F,
+                                          float4 *dst, int ss) {
+  uint32_t nt0, np0, nt1, np1;
+  G::unpack((uint32_t)(w0 >> 32), (uint32_t)w0, nt0, np0);
+  G::unpack((uint32_t)(w1 >> 32), (uint32_t)w1, nt1, np1);
+  cp_async16(dst + 2 * ss, F.phi_tab + min((int)np0, G::M - (int)np0));
+  cp_async16(dst + 3 * ss, F.phi_tab + min((int)np1, G::M - (int)np1));
 }
 
 // Decodes two words through the fast path, falling back per element.  PT:

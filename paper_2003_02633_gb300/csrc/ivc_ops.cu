@@ -393,7 +393,10 @@ __global__ void __launch_bounds__(256, 3) k_compress_fast(const __grid_constant_
 }
 
 // Decompress n words (primary layout) to AoS FP32, two per thread.  Requires
-// a 16-byte aligned w and an 8-byte aligned xyz.
+// a 16-byte aligned w and an 8-byte aligned xyz.  With the per-code phi^
+// table, each word's phi^ entry is copied into shared memory by cp.async one
+// iteration ahead (a decode alone has too little work to hide a direct L2
+// gather); otherwise phi^ comes from the shared head table.
 template <class G>
 __global__ void __launch_bounds__(256, 2) k_decompress_fast(const __grid_constant__ DevFormat F,
                                                          const uint64_t *__restrict__ w,
@@ -404,17 +407,45 @@ __global__ void __launch_bounds__(256, 2) k_decompress_fast(const __grid_constan
   const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(w);
   float2 *v2 = reinterpret_cast<float2 *>(xyz);
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (G::MAP != MAP_TANH && F.phi_tab) {
+    // per-code phi^ entries by cp.async one iteration ahead (two buffers of
+    // 4 slots per thread, slots 2 and 3 used), words two iterations ahead
+    extern __shared__ TabEntry ivc_smem_tab[];
+    float4 *sbuf = reinterpret_cast<float4 *>(ivc_smem_tab + fast::fast_ntab<G>(F));
+    const int ss = blockDim.x, t = threadIdx.x;
+    ulonglong2 cw = i0 < n2 ? __ldcs(w2 + i0) : make_ulonglong2(0ull, 0ull);
+    ulonglong2 nw = i0 + stride < n2 ? __ldcs(w2 + i0 + stride) : make_ulonglong2(0ull, 0ull);
+    fast::stage_phi<G>(cw.x, cw.y, F, sbuf + t, ss);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    int buf = 0;
+    for (int64_t i = i0; i < n2; i += stride) {
+      const ulonglong2 ww = cw;
+      cw = nw;
+      if (i + 2 * stride < n2) nw = __ldcs(w2 + i + 2 * stride);
+      fast::stage_phi<G>(cw.x, cw.y, F, sbuf + (buf ^ 1) * 4 * ss + t, ss);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      const fast::Staged sg{sbuf + buf * 4 * ss + t, ss};
+      buf ^= 1;
+      float2 X, Y, Z;
+      fast::decode2_full<G, true>(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z, &sg);
+      __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
+      __stcs(v2 + 3 * i + 1, make_float2(Z.x, X.y));
+      __stcs(v2 + 3 * i + 2, make_float2(Y.y, Z.y));
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else {
   ulonglong2 nw = i0 < n2 ? __ldcs(w2 + i0) : make_ulonglong2(0ull, 0ull);  // next words
   for (int64_t i = i0; i < n2; i += stride) {
     const ulonglong2 ww = nw;
     if (i + stride < n2) nw = __ldcs(w2 + i + stride);
     float2 X, Y, Z;
-    // table-free decode: a launch of decodes alone is faster with the phi^
-    // head table in shared memory than with the per-code table (measured)
+    // no per-code table: phi^ from the shared head table
     fast::decode2_full<G, false>(ww.x, ww.y, F, tab_t, tab_p, X, Y, Z);
     __stcs(v2 + 3 * i, make_float2(X.x, Y.x));
     __stcs(v2 + 3 * i + 1, make_float2(Z.x, X.y));
     __stcs(v2 + 3 * i + 2, make_float2(Y.y, Z.y));
+  }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t i = n - 1;
@@ -626,8 +657,9 @@ size_t kernel_smem_bytes(const DevFormat &F, int map, int kind, int block) {
   // the tanh map's fused add / axpy stage their decoder's table entries (two
   // buffers of 8 16-byte slots per thread)
   const bool staged = (kind == K_ADD_FAST || kind == K_AXPY_FAST) && map == MAP_TANH;
+  const bool dstaged = kind == K_DECOMPRESS_FAST && map != MAP_TANH && F.phi_tab != nullptr;
   return tabs + (queue ? (size_t)(block / 32) * fast::kQueueCap * sizeof(fast::PendItem) : 0) +
-         (staged ? (size_t)block * 16 * 16 : 0);
+         (staged ? (size_t)block * 16 * 16 : 0) + (dstaged ? (size_t)block * 8 * 16 : 0);
 }
 
 #define IVC_DISPATCH_MAP(map, KERNEL, ...)                                                    \
