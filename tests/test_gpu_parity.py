@@ -207,6 +207,23 @@ def test_tanh_add_axpy_many_iterations():
                 "tanh axpy in place, many iterations")
 
 
+@pytest.mark.parametrize("name", ["primary", "L1717", "L1617", "fracsplit"])
+def test_decompress_many_iterations(name):
+    """The fast decompress copies each word's phi^ table entry into shared
+    memory one iteration ahead (cp.async, two buffers): 2^21 + 3 words give
+    every thread about a dozen iterations and an odd tail; the decoded
+    vectors match the oracle's (within one ulp, bit for bit almost always, as
+    for the other decompress tests)."""
+    fo, fg = formats(name)
+    a, _ = synth.roundtrip_inputs((1 << 21) + 3, seed=73)
+    w = O.compress(fo, a)
+    with np.errstate(invalid="ignore", over="ignore"):
+        want = O.decompress(fo, w)
+    got = ivc.decompress(fg, _words_dev(w)).cpu().numpy()
+    same = check_decoded(got, want, f"{name} decompress, many iterations")
+    assert same > 0.9999, f"{name}: {1 - same:.2e} of the decodes differ from the oracle"
+
+
 def test_counts_match_oracle():
     fo, fg = formats("primary")
     x = synth.precision_vectors(1 << 16, seed=11)
